@@ -1,0 +1,182 @@
+"""One time step of the filtered SELBM, written step by step in the paper's order
+(Sec. 2, summary list at the end of Sec. 2.4):
+
+1. moments rho = sum f_bar, rho u = sum e f_bar                 (Eqs. pressure, momentum)
+2. BGK collision with the higher-order force F**                  (collision equation, Sec. 2.1)
+3. streaming d f_bar/dt = L(f_bar) by SSPRK3 with F* and the
+   flux bounce-back boundary flux                                 (Eqs. full, entire; Sec. 2.2.2)
+4. explicit modal filter on every f_alpha                         (Sec. 2.4)
+5. moments for output
+
+The state lives on unique (assembled) GLL nodes: f[Q, G].  The
+continuous-Galerkin coupling is the assembly (direct stiffness summation) of
+the element contributions, divided by the assembled lumped mass.
+
+Readings of the paper taken here (each one listed in the design doc):
+* L f = M^{-1}(R (n.j) - C f) + F*: the identity term printed in the
+  operator definition is dropped (it would create mass).
+* "3rd order SSP RK" is the Shu-Osher three-stage scheme.
+* The geometric factor G_lk = rho rho rho J dr_l/dx_k (chain rule).
+* No flux at interior element faces; assembly only (continuous Galerkin).
+* The filter is applied once per step after the last stage, element by
+  element; at shared nodes the copies agree in exact arithmetic and the
+  oracle stores their mean.
+* F = rho g with rho from the step's moments, frozen through the stages.
+"""
+import numpy as np
+
+from . import geometry as geo
+from . import gll
+from .lattice import CS2, equilibrium, force_split, lattice
+
+
+class OracleSELBM:
+    """Plain FP64 filtered SELBM on unique GLL nodes."""
+
+    def __init__(self, mesh, lattice_name, N, nu, cfl=0.5, dt=None, rho0=1.0,
+                 filt=None, body_accel=None):
+        self.mesh, self.N, self.dim = mesh, N, mesh.dim
+        self.e, self.t, self.opp = lattice(lattice_name)
+        self.Q = len(self.t)
+        self.rho0 = rho0
+        self.xi = gll.gll_nodes(N)
+        self.w = gll.gll_weights(N, self.xi)
+        self.D = gll.derivative_matrix(self.xi)
+        self.X = geo.element_nodes(mesh, self.xi)
+        self.E, self.Np = self.X.shape[0], self.X.shape[1]
+        self.dxdr, self.J, self.drdx, self.wJ = geo.metrics(self.X, self.D, N, self.dim, self.w)
+        if np.any(self.J <= 0):
+            raise ValueError("non-positive Jacobian")
+        self.glo = geo.global_numbering(self.X, mesh)
+        self.G = int(self.glo.max()) + 1
+        self.mass = np.zeros(self.G)
+        np.add.at(self.mass, self.glo.ravel(), self.wJ.ravel())
+        self.copies = np.bincount(self.glo.ravel(), minlength=self.G)
+        _, first = np.unique(self.glo.ravel(), return_index=True)
+        self.Xg = self.X.reshape(-1, self.dim)[first]          # coordinates of each unique node
+        self.walls = geo.wall_faces(mesh, self.drdx, self.J, self.w, N)
+        self.dt = dt if dt is not None else cfl * geo.min_node_spacing(self.X, N, self.dim)
+        self.lam = nu / CS2                                      # nu = lambda cs^2 (Sec. 2.1)
+        self.tau = self.lam / self.dt                            # tau = lambda / dt
+        self.nu = nu
+        f = filt or {"shape": 0, "gamma": 0.0, "kc": float(N), "p": 8.0}
+        self.set_filter(f)
+        g = np.zeros(self.dim) if body_accel is None else np.asarray(body_accel, float)[: self.dim]
+        self.g = g
+
+    # ------------------------------------------------------------------ setup
+    def set_filter(self, f):
+        self.filt = dict(f)
+        sig = gll.filter_sigma(self.N, int(f["shape"]), float(f["gamma"]), float(f["kc"]), float(f.get("p", 8.0)))
+        self.sigma = sig
+        self.Fmat = gll.filter_matrix(self.N, self.xi, sig)
+        self.filter_on = float(f["gamma"]) != 0.0 and float(f["kc"]) < self.N
+
+    # --------------------------------------------------------------- helpers
+    def to_local(self, fg):
+        """Unique-node field [..., G] -> element-local copies [..., E, Np]."""
+        return fg[..., self.glo]
+
+    def moments(self, f):
+        """rho = sum_alpha f_bar_alpha, u = (sum_alpha e_alpha f_bar_alpha) / rho (Eqs. pressure, momentum)."""
+        rho = f.sum(axis=0)
+        j = self.e.T.astype(float) @ f                    # [d, n]
+        return rho, (j / rho).T                           # rho [n], u [n, d]
+
+    def initial_state(self, rho, u):
+        """f_bar at rest in equilibrium: f = f^eq, so f_bar = f^eq - dt/2 F** (Sec. 2.1)."""
+        F = rho[:, None] * self.g[None, :]
+        _, Fss = force_split(self.e, self.t, u, F)
+        return equilibrium(self.e, self.t, rho, u) - 0.5 * self.dt * Fss
+
+    def initial_state_from(self, init):
+        rho, u = init(self.Xg)
+        return self.initial_state(rho, u[:, : self.dim])
+
+    # -------------------------------------------------------------- collision
+    def collide(self, f):
+        """f* = f_bar - (f_bar - f_bar^eq)/(tau + 1/2) + dt F**, f_bar^eq = f^eq - dt/2 F** (Sec. 2.1).
+
+        Returns (f*, F*) with F* the leading-order force for the streaming step."""
+        rho, u = self.moments(f)
+        F = rho[:, None] * self.g[None, :]
+        Fstar, Fss = force_split(self.e, self.t, u, F)
+        feq_bar = equilibrium(self.e, self.t, rho, u) - 0.5 * self.dt * Fss
+        fstar = f - (f - feq_bar) / (self.tau + 0.5) + self.dt * Fss
+        return fstar, Fstar
+
+    # ------------------------------------------------------------- streaming
+    def element_contribution(self, f):
+        """Weighted element contribution c[Q, E, Np] of -C f + R (n.j) (Eqs. advection2, entire).
+
+        Interior:  c = -wJ sum_l (sum_k e_k dr_l/dx_k) (D_l f)        (C = phi^T e G D* phi)
+        Wall face: c += w_s J_s (n.e_alpha) [f_alpha - f_beta - 2 t_alpha rho0 (e_alpha.u_b)/cs2]
+                   for n.e_alpha < 0 (flux bounce-back, Sec. 2.2.1).
+        """
+        fl = self.to_local(f)                                       # [Q, E, Np]
+        grads = [geo.apply_axis(self.D, fl, l, self.N, self.dim) for l in range(self.dim)]
+        c = np.zeros_like(fl)
+        ef = self.e.astype(float)
+        for a in range(self.Q):
+            adv = np.zeros((self.E, self.Np))
+            for l in range(self.dim):
+                coef = (self.drdx[:, :, l, :] * ef[a][None, None, :]).sum(-1)   # sum_k e_k dr_l/dx_k
+                adv += coef * grads[l][a]
+            c[a] = -self.wJ * adv
+        for (el, nodes, n, wsJs, wid) in self.walls:
+            ub = self.mesh.wall_velocity[wid - 1][: self.dim]
+            ne = n @ ef.T                                           # [nf, Q]
+            for a in range(self.Q):
+                b = self.opp[a]
+                inc = ne[:, a] < 0.0
+                jump = fl[a, el, nodes] - fl[b, el, nodes] - 2.0 * self.t[a] * self.rho0 * (ef[a] @ ub) / CS2
+                c[a, el, nodes] += np.where(inc, wsJs * ne[:, a] * jump, 0.0)
+        return c
+
+    def rhs(self, f, Fstar):
+        """L(f) = M^{-1} assemble(c) + F* on unique nodes (continuous Galerkin)."""
+        c = self.element_contribution(f)
+        R = np.zeros((self.Q, self.G))
+        for a in range(self.Q):
+            np.add.at(R[a], self.glo.ravel(), c[a].ravel())       # ascending copy order
+        return R / self.mass[None, :] + Fstar
+
+    def ssprk3(self, f0, Fstar):
+        """Shu-Osher SSPRK3 (Sec. 2.2.2)."""
+        dt = self.dt
+        f1 = f0 + dt * self.rhs(f0, Fstar)
+        f2 = 0.75 * f0 + 0.25 * (f1 + dt * self.rhs(f1, Fstar))
+        return f0 / 3.0 + 2.0 / 3.0 * (f2 + dt * self.rhs(f2, Fstar))
+
+    # ----------------------------------------------------------------- filter
+    def apply_filter(self, f):
+        """(F x F (x F)) f_alpha element by element (Sec. 2.4); shared nodes take the mean of their copies."""
+        if not self.filter_on:
+            return f
+        fl = self.to_local(f)
+        for l in range(self.dim):
+            fl = geo.apply_axis(self.Fmat, fl, l, self.N, self.dim)
+        out = np.zeros_like(f)
+        for a in range(self.Q):
+            np.add.at(out[a], self.glo.ravel(), fl[a].ravel())
+        return out / self.copies[None, :]
+
+    # ------------------------------------------------------------------- step
+    def step(self, f):
+        f0, Fstar = self.collide(f)
+        f3 = self.ssprk3(f0, Fstar)
+        return self.apply_filter(f3)
+
+    def run(self, f, nsteps):
+        for _ in range(nsteps):
+            f = self.step(f)
+        return f
+
+    # ------------------------------------------------------------ diagnostics
+    def integrals(self, f):
+        """Quadrature integrals: mass sum M rho, momentum sum M rho u, KE = sum M rho0 |u|^2 / 2."""
+        rho, u = self.moments(f)
+        mass = float((self.mass * rho).sum())
+        mom = (self.mass[:, None] * rho[:, None] * u).sum(0)
+        ke = float(0.5 * self.rho0 * (self.mass * (u * u).sum(1)).sum())
+        return mass, mom, ke

@@ -1,0 +1,219 @@
+"""Pins of the oracle's operator and time step against closed forms:
+advection accuracy on affine and curved meshes, discrete conservation (P3),
+SSPRK3 order, collision invariants, unsteady Couette series (P6), planar
+Poiseuille parabola and slip trend (P7), 2D Taylor-Green decay (P8)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.lattice import CS2
+from oracle.selbm import OracleSELBM
+
+
+def _smooth(X, k=1.0):
+    return np.sin(k * X[:, 0] + 0.3) * np.cos(k * X[:, 1] - 0.2) * (np.cos(k * X[:, 2]) if X.shape[1] == 3 else 1.0)
+
+
+def _grad_smooth(X, k=1.0):
+    x, y = X[:, 0], X[:, 1]
+    cz = np.cos(k * X[:, 2]) if X.shape[1] == 3 else 1.0
+    gx = k * np.cos(k * x + 0.3) * np.cos(k * y - 0.2) * cz
+    gy = -k * np.sin(k * x + 0.3) * np.sin(k * y - 0.2) * cz
+    if X.shape[1] == 2:
+        return np.stack([gx, gy], 1)
+    gz = -k * np.sin(k * x + 0.3) * np.cos(k * y - 0.2) * np.sin(k * X[:, 2])
+    return np.stack([gx, gy, gz], 1)
+
+
+def test_advection_operator_periodic_box():
+    """Assembled L f_alpha = -e_alpha . grad f_alpha to spectral accuracy; wrong
+    sign, transposed D or wrong metric would fail."""
+    L = 2 * np.pi
+    mesh = W.box_mesh((3, 3), (0, 0), (L, L), (True, True))
+    o = OracleSELBM(mesh, "D2Q9", 10, nu=0.01)
+    f = np.tile(_smooth(o.Xg)[None], (o.Q, 1))
+    r = o.rhs(f, np.zeros_like(f))
+    exact = -(o.e.astype(float) @ _grad_smooth(o.Xg).T)
+    assert np.abs(r - exact).max() < 1e-4
+
+
+def test_advection_operator_curved_pipe():
+    """Curved isoparametric metrics: interior (non-wall) nodes match -e . grad f."""
+    mesh = W.pipe_mesh(n_core=4, n_radial=3, n_axial=2, length=2 * np.pi)
+    o = OracleSELBM(mesh, "D3Q19", 7, nu=0.01)
+    f = np.tile(_smooth(o.Xg)[None], (o.Q, 1))
+    r = o.rhs(f, np.zeros_like(f))
+    exact = -(o.e.astype(float) @ _grad_smooth(o.Xg).T)
+    interior = np.linalg.norm(o.Xg[:, :2], axis=1) < 0.999
+    assert np.abs(r[:, interior] - exact[:, interior]).max() < 2e-3
+
+
+def test_discrete_mass_conservation_operator():
+    """On a periodic affine mesh sum_g M_g L(f)_g = 0 for any continuous f (P3)."""
+    mesh = W.box_mesh((3, 2, 2), (0, 0, 0), (1, 1, 1), (True, True, True))
+    o = OracleSELBM(mesh, "D3Q27", 4, nu=0.01)
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((o.Q, o.G))
+    r = o.rhs(f, np.zeros_like(f))
+    assert np.abs(r @ o.mass).max() < 1e-12 * np.abs(f).max() * o.mass.sum()
+
+
+def test_collision_invariants():
+    mesh = W.box_mesh((2, 2), (0, 0), (1, 1), (True, True))
+    o = OracleSELBM(mesh, "D2Q9", 4, nu=0.01, body_accel=[1e-3, -2e-3])
+    rng = np.random.default_rng(4)
+    rho = 1 + 0.01 * rng.standard_normal(o.G)
+    u = 0.03 * rng.standard_normal((o.G, 2))
+    f = o.initial_state(rho, u) + 1e-3 * rng.standard_normal((o.Q, o.G)) * o.t[:, None]
+    fs, Fs = o.collide(f)
+    ef = o.e.astype(float)
+    assert np.abs(fs.sum(0) - f.sum(0)).max() < 1e-14
+    assert np.abs(ef.T @ fs - ef.T @ f).max() < 1e-14
+
+
+def test_collision_relaxation_rate():
+    """Without force the non-equilibrium part decays by 1 - 1/(tau + 1/2) per collision."""
+    mesh = W.box_mesh((2, 2), (0, 0), (1, 1), (True, True))
+    o = OracleSELBM(mesh, "D2Q9", 3, nu=0.02)
+    rng = np.random.default_rng(5)
+    f = o.initial_state(np.ones(o.G), 0.02 * rng.standard_normal((o.G, 2)))
+    neq = 1e-4 * rng.standard_normal((o.Q, o.G)) * o.t[:, None]
+    neq -= neq.sum(0) * o.t[:, None]                      # no mass
+    neq -= (o.e.astype(float) @ (o.e.astype(float).T @ neq)) * o.t[:, None] / CS2   # no momentum
+    fs, _ = o.collide(f + neq)
+    assert np.abs((fs - f) - (1 - 1 / (o.tau + 0.5)) * neq).max() < 1e-15
+
+
+def test_momentum_growth_with_body_force():
+    """Periodic affine mesh: each step adds dt * sum M rho g of momentum (P3)."""
+    mesh = W.box_mesh((2, 2), (0, 0), (1, 1), (True, True))
+    g = np.array([2e-4, -1e-4])
+    o = OracleSELBM(mesh, "D2Q9", 4, nu=0.01, body_accel=g,
+                    filt={"shape": 0, "gamma": 0.1, "kc": 2.0})
+    f = o.initial_state_from(W.shear_layer_init(U0=0.02, kappa=5.0))
+    for _ in range(3):
+        mass0, mom0, _ = o.integrals(f)
+        rho, _ = o.moments(f)
+        f = o.step(f)
+        mass1, mom1, _ = o.integrals(f)
+        assert abs(mass1 - mass0) < 1e-13
+        assert np.abs(mom1 - mom0 - o.dt * (o.mass * rho).sum() * g).max() < 1e-15
+
+
+def test_ssprk3_third_order():
+    """Pure advection (no collision, no filter): temporal error ~ dt^3 (P9)."""
+    L = 2 * np.pi
+    mesh = W.box_mesh((2, 2), (0, 0), (L, L), (True, True))
+    o = OracleSELBM(mesh, "D2Q9", 8, nu=0.01)
+    f0 = np.tile(np.sin(o.Xg[:, 0] + 0.1)[None] * np.cos(o.Xg[:, 1])[None], (o.Q, 1))
+    z = np.zeros_like(f0)
+    T = 0.4
+
+    def run(n):
+        dt_save = o.dt
+        o.dt = T / n
+        f = f0.copy()
+        for _ in range(n):
+            f = o.ssprk3(f, z)
+        o.dt = dt_save
+        return f
+
+    ref = run(256)
+    errs = [np.abs(run(n) - ref).max() for n in (8, 16, 32)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(2.7 < r < 3.3 for r in rates), rates
+
+
+def test_couette_series():
+    """Unsteady Couette (P6, config: 8x4 quads, N=4, D2Q9, nu=0.002, U0=0.01, 2000 steps)."""
+    c = W.couette_case()
+    o = OracleSELBM(c.mesh, c.lattice, c.order, c.nu, cfl=c.cfl, filt=c.filt)
+    f = o.run(o.initial_state_from(c.init), c.steps)
+    _, u = o.moments(f)
+    T = c.steps * o.dt
+    y = o.Xg[:, 1]
+    ua = c.U0 * y
+    for n in range(1, 201):
+        ua += 2 * c.U0 * (-1) ** n / (n * np.pi) * np.sin(n * np.pi * y) * np.exp(-n * n * np.pi ** 2 * c.nu * T)
+    assert np.abs(u[:, 0] - ua).max() < 1e-3 * c.U0
+    assert np.abs(u[:, 1]).max() < 1e-4 * c.U0
+
+
+def _poiseuille(cfl, tau=0.4, steps=300):
+    Ne, N = 4, 8
+    mesh = W.box_mesh((Ne, Ne), (0, 0), (1, 1), (True, False), walls={2: 1, 3: 1}, wall_velocity=[[0, 0]])
+    probe = OracleSELBM(mesh, "D2Q9", N, nu=1.0, cfl=cfl)
+    nu = tau * probe.dt * CS2                     # tau = lambda/dt, nu = lambda cs2
+    umax = 0.1 / math.sqrt(3) * math.sqrt(CS2)    # Ma = umax/cs = 0.1/sqrt(3)
+    G = 8 * nu * umax                             # rho0 = 1, L = 1
+    o = OracleSELBM(mesh, "D2Q9", N, nu=nu, cfl=cfl, body_accel=[G, 0.0])
+    f = o.initial_state_from(W.poiseuille_init(G, nu))
+    f = o.run(f, steps)
+    _, u = o.moments(f)
+    y = o.Xg[:, 1]
+    ua = G / (2 * nu) * y * (1 - y)
+    wall = (np.abs(y) < 1e-12)
+    return np.abs(u[:, 0] - ua).max() / umax, np.abs(u[wall, 0]).max() / umax
+
+
+def test_poiseuille_parabola_and_slip_trend():
+    """Started on the analytic parabola (P7), the profile stays within 1% of u_max;
+    the wall slip shrinks when dt shrinks at fixed tau (paper Sec. 3.3)."""
+    err_a, slip_a = _poiseuille(0.5)
+    err_b, slip_b = _poiseuille(0.25, steps=600)
+    assert err_a < 1e-2 and err_b < 1e-2
+    assert slip_b < slip_a
+
+
+def test_taylor_green_2d_decay():
+    """Low-Re 2D Taylor-Green (P8): the mode amplitude decays as exp(-2 nu t) with
+    nu = lambda cs2.  The rate is taken between two later times so that the
+    start-up transient of an equilibrium initial state (a delay of order
+    lambda) drops out; the velocity field keeps the sin x cos y shape.  nu is
+    small enough (k^2 cs2 lambda^2 ~ 6e-4) that the BGK equation's own
+    higher-order correction to the shear decay stays below the tolerance.  A
+    relaxation rate of 1/tau instead of 1/(tau + 1/2) would be off by ~100%."""
+    L = 2 * np.pi
+    mesh = W.box_mesh((4, 4), (0, 0), (L, L), (True, True))
+    U0, nu = 0.01, 0.01
+    o = OracleSELBM(mesh, "D2Q9", 6, nu=nu, cfl=0.5)
+    X = o.Xg
+    mode = np.sin(X[:, 0]) * np.cos(X[:, 1])
+
+    def amp(f):
+        _, u = o.moments(f)
+        return (o.mass * u[:, 0] * mode).sum() / (o.mass * mode * mode).sum(), u
+
+    f = o.run(o.initial_state_from(W.tgv2d_init(U0)), 30)
+    a1, _ = amp(f)
+    f = o.run(f, 60)
+    a2, u = amp(f)
+    rate = math.log(a1 / a2) / (60 * o.dt)
+    assert abs(rate - 2 * nu) < 1.5e-3 * 2 * nu, rate
+    assert np.abs(u[:, 0] - a2 * mode).max() < 1e-2 * a2
+    assert np.abs(u[:, 1] + a2 * np.cos(X[:, 0]) * np.sin(X[:, 1])).max() < 1e-2 * a2
+
+
+def test_filter_continuity_and_mass():
+    """Filtered copies of shared nodes agree; filtering conserves mass on affine meshes."""
+    mesh = W.box_mesh((3, 3), (0, 0), (1, 1), (True, True))
+    o = OracleSELBM(mesh, "D2Q9", 6, nu=0.01, filt={"shape": 1, "gamma": 0.3, "kc": 3.0})
+    rng = np.random.default_rng(6)
+    f = rng.standard_normal((o.Q, o.G))
+    fl = o.to_local(f)
+    from oracle import geometry as geo
+    for l in range(2):
+        fl = geo.apply_axis(o.Fmat, fl, l, o.N, 2)
+    spread = np.zeros((o.Q, o.G))
+    base = np.full((o.Q, o.G), np.nan)
+    for idx in range(o.E * o.Np):
+        g = o.glo.ravel()[idx]
+        v = fl.reshape(o.Q, -1)[:, idx]
+        if np.isnan(base[0, g]):
+            base[:, g] = v
+        spread[:, g] = np.maximum(spread[:, g], np.abs(v - base[:, g]))
+    assert spread.max() < 1e-13
+    ff = o.apply_filter(f)
+    assert np.abs(ff @ o.mass - f @ o.mass).max() < 1e-12
