@@ -1,0 +1,179 @@
+/*
+ * selbm.h - C ABI of the GB300 filtered spectral-element lattice Boltzmann
+ * library (method of Zhao, Patel, Lin, Min, Lee, "A flux bounce-back scheme for
+ * the filtered Spectral Element Lattice Boltzmann Method", arXiv 2509.19171).
+ *
+ * One handle = one simulation on one GPU.  Every entry point returns an int
+ * status (SELBM_OK = 0, negative = error; selbm_last_error() gives the text)
+ * unless stated otherwise.  All work is enqueued on the CUDA stream given to
+ * selbm_create(); calls that return data to the host synchronise that stream.
+ * Input arrays are copied; the caller keeps ownership of every pointer it
+ * passes.  Output buffers are caller-owned and must be large enough.
+ *
+ * Population order (the index alpha of every state array): velocities sorted
+ * by speed class |e|^2 = 0, 1, 2, 3 and, inside a class, by the ternary code
+ * (e_x+1) + 3 (e_y+1) + 9 (e_z+1) ascending.  selbm_lattice_table() returns
+ * the table.  Node order inside an element: i + (N+1) j + (N+1)^2 k, r index
+ * fastest (Sec. 2.2 of the paper).
+ */
+#ifndef SELBM_H
+#define SELBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct selbm selbm_t; /* opaque; owned by the library */
+
+enum {
+  SELBM_OK = 0,
+  SELBM_ERR_ARG = -1,       /* bad argument (NULL, size out of range, unsupported option) */
+  SELBM_ERR_MESH = -2,      /* non-positive Jacobian, unmatched periodic nodes, bad tags */
+  SELBM_ERR_CUDA = -3,      /* a CUDA call failed (text in selbm_last_error) */
+  SELBM_ERR_NONFINITE = -4, /* the state holds NaN or Inf */
+  SELBM_ERR_TIMEOUT = -5,   /* a bounded device wait gave up */
+  SELBM_ERR_STATE = -6      /* call out of order (e.g. step before init) */
+};
+
+enum { SELBM_D2Q9 = 0, SELBM_D3Q19 = 1, SELBM_D3Q27 = 2 };
+
+/* Storage / arithmetic form of the hot path. */
+enum {
+  SELBM_FP64 = 0,   /* state f stored and updated in FP64 */
+  SELBM_FP32DEV = 1 /* deviations g = f - t_alpha rho0 stored and updated in FP32;
+                       metrics and matrices built in FP64 */
+};
+
+/*
+ * Conforming quad (dim 2) / hex (dim 3) mesh given by element corners.
+ *  verts[e][c][k]   corner c = a + 2b (+4g), a,b,g in {0,1} <-> r,s(,t) = -1/+1
+ *  curved[e][f]     1: face f lies on the circle/cylinder x^2 + y^2 = radius^2
+ *                   (axis z); the edge(s) of that face in the x-y plane are
+ *                   circular arcs with the angle linear in the reference
+ *                   coordinate; curved 3D elements are extrusions along z.
+ *                   Face ids: 0 r=-1, 1 r=+1, 2 s=-1, 3 s=+1, 4 t=-1, 5 t=+1.
+ *                   May be NULL (all flat).
+ *  face_bc[e][f]    0: interior or periodic face; k >= 1: wall k (flux
+ *                   bounce-back, Sec. 2.2.1) moving with wall_velocity[k-1].
+ *                   May be NULL (no walls).
+ *  period[k]        periodic length along axis k, 0 if not periodic.
+ *  origin[k]        domain origin along axis k (for periodic wrapping).
+ * The element map is the Gordon-Hall blend of the (straight or arc) edges in
+ * (r, s), linear in t; GLL nodes that coincide (modulo periods) are one node.
+ */
+typedef struct {
+  int32_t dim;
+  int32_t nelem;
+  const double *verts;
+  const int32_t *curved;
+  const int32_t *face_bc;
+  const double *period;
+  const double *origin;
+  int32_t nwalls;
+  const double *wall_velocity; /* [nwalls][dim] */
+  double radius;
+} selbm_mesh;
+
+/*
+ * Explicit modal filter (Sec. 2.4): sigma_k = 1 for k <= kc, else
+ *  shape 0 (paper): 1 - gamma r^2;  shape 1: (1 - gamma)^(r^p);  r = (k-kc)/(N-kc).
+ * Applied to every population, element by element, once per step after the
+ * last Runge-Kutta stage, in the hierarchical basis 1, xi, L_k - L_{k-2}.
+ * gamma = 0 disables it.  kc must satisfy 1 <= kc < N (real values allowed).
+ */
+typedef struct {
+  int32_t shape;
+  double gamma;
+  double kc;
+  double p;
+} selbm_filter;
+
+typedef struct {
+  int32_t lattice;        /* SELBM_D2Q9 / D3Q19 / D3Q27 (dim must match the mesh) */
+  int32_t order;          /* polynomial order N, 2 <= N <= 12 */
+  double nu;              /* kinematic viscosity; lambda = nu / cs^2, tau = lambda / dt */
+  double dt;              /* > 0: time step; <= 0: dt = cfl * smallest GLL node spacing */
+  double cfl;
+  double rho0;            /* reference density of the wall term and of the FP32 deviations */
+  int32_t precision;      /* SELBM_FP64 or SELBM_FP32DEV */
+  selbm_filter filter;
+  double body_accel[3];   /* g: body force F = rho g (Sec. 3.5), split into F* and F** */
+} selbm_params;
+
+/*
+ * Build the handle: GLL tables, element map, metrics (all FP64), global node
+ * numbering, assembly map, wall tables; allocate device state.  The hot path
+ * runs on `cuda_stream` (a cudaStream_t, NULL = legacy default stream).
+ * Errors: SELBM_ERR_ARG, SELBM_ERR_MESH, SELBM_ERR_CUDA; *out is NULL then.
+ */
+int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_stream, selbm_t **out);
+void selbm_destroy(selbm_t *h);
+/* Text of the last error on this handle (or of the last failed create when h is NULL). */
+const char *selbm_last_error(const selbm_t *h);
+
+/*
+ * Sizes and scalars: out_i[0..7] = E, Np, Q, G (unique nodes), dim, N,
+ * precision, steps taken; out_d[0..3] = dt, tau, lambda, time.
+ */
+int selbm_info(const selbm_t *h, int64_t out_i[8], double out_d[4]);
+/* Lattice table: e[Q][3] (zero-padded in 2D), t[Q], opposite[Q]. */
+int selbm_lattice_table(const selbm_t *h, int32_t *e, double *t, int32_t *opp);
+/* Physical coordinates of every local node, host buffer [E][Np][dim]. */
+int selbm_node_coords(const selbm_t *h, double *xyz);
+
+/*
+ * Initial state f_bar = f^eq(rho, u) - dt/2 F** (Sec. 2.1, f at equilibrium).
+ * rho [E][Np], u [E][Np][dim]; host pointers, or device pointers when
+ * on_device = 1.  Copies of a shared node take the value of its first copy
+ * (lowest e, then lowest local index).
+ */
+int selbm_init(selbm_t *h, const double *rho, const double *u, int on_device);
+/* Set / read the full state f_bar, layout [Q][E][Np] FP64 (read: filtered, as after a step). */
+int selbm_set_state(selbm_t *h, const double *f, int on_device);
+int selbm_get_state(selbm_t *h, double *f, int on_device);
+
+/*
+ * Advance nsteps time steps (Sec. 2, summary list): BGK collision with F**,
+ * three Shu-Osher SSPRK3 stages of the weak advection with F* and the flux
+ * bounce-back wall flux, assembly of shared nodes, explicit filter.
+ * Asynchronous: enqueues the work and returns.  Errors: SELBM_ERR_STATE
+ * (not initialised), SELBM_ERR_CUDA (launch failure).
+ */
+int selbm_step(selbm_t *h, int64_t nsteps);
+
+/* Density and velocity rho = sum f_bar, rho u = sum e f_bar (Eqs. pressure, momentum)
+ * at every local node: rho [E][Np], u [E][Np][dim]. */
+int selbm_moments(selbm_t *h, double *rho, double *u, int on_device);
+
+/* Replace the filter (Sec. 2.4); takes effect from the next step. */
+int selbm_set_filter(selbm_t *h, const selbm_filter *filter);
+/* Replace the body acceleration g (F = rho g). */
+int selbm_set_body_force(selbm_t *h, const double g[3]);
+
+/*
+ * Diagnostics of the current (filtered) state, FP64 quadrature sums:
+ * out[0] mass = sum_g M_g rho, out[1..3] momentum sum M rho u,
+ * out[4] kinetic energy sum M rho0 |u|^2 / 2, out[5] 0 (reserved), out[6] dt, out[7] time.
+ * Returns SELBM_ERR_NONFINITE if the state holds NaN/Inf.
+ */
+int selbm_diagnostics(selbm_t *h, double out[8]);
+
+/*
+ * Dry run of selbm_create's host setup, without touching the GPU: validates
+ * the mesh and reports out_i[0..5] = E, Np, Q, G (unique nodes), Gb (nodes on
+ * element boundaries), affine (1 if every element has constant metrics);
+ * out_d[0..3] = smallest GLL node spacing, sum of the assembled lumped mass
+ * (domain measure), number of wall-face nodes, sum of wall surface weights.
+ * Errors as selbm_create (SELBM_ERR_ARG / SELBM_ERR_MESH), text in selbm_last_error(NULL).
+ */
+int selbm_mesh_check(const selbm_mesh *mesh, int32_t lattice, int32_t order, int64_t out_i[6], double out_d[4]);
+
+/* Block until all work on the handle's stream is done; returns the first CUDA error seen. */
+int selbm_sync(selbm_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SELBM_H */

@@ -1,0 +1,265 @@
+"""Python binding of libselbm.so (include/selbm.h): the filtered spectral-element
+lattice Boltzmann method with flux bounce-back walls on one GB300 GPU.
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+PyTorch supplies device memory and the CUDA stream.  There is no CPU fallback:
+if ``libselbm.so`` is missing this module raises on import of the library
+(build it with ``python -m paper_2509_19171_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libselbm.so")
+
+D2Q9, D3Q19, D3Q27 = 0, 1, 2
+LATTICES = {"D2Q9": D2Q9, "D3Q19": D3Q19, "D3Q27": D3Q27}
+FP64, FP32DEV = 0, 1
+ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_MESH", -3: "ERR_CUDA", -4: "ERR_NONFINITE", -5: "ERR_TIMEOUT", -6: "ERR_STATE"}
+
+# functions declared in include/selbm.h (checked by the ABI test)
+EXPORTS = ["selbm_create", "selbm_destroy", "selbm_last_error", "selbm_info", "selbm_lattice_table",
+           "selbm_node_coords", "selbm_init", "selbm_set_state", "selbm_get_state", "selbm_step",
+           "selbm_moments", "selbm_set_filter", "selbm_set_body_force", "selbm_diagnostics", "selbm_sync",
+           "selbm_mesh_check"]
+
+
+class SelbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class MeshC(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("nelem", C.c_int32), ("verts", C.POINTER(C.c_double)),
+                ("curved", C.POINTER(C.c_int32)), ("face_bc", C.POINTER(C.c_int32)),
+                ("period", C.POINTER(C.c_double)), ("origin", C.POINTER(C.c_double)),
+                ("nwalls", C.c_int32), ("wall_velocity", C.POINTER(C.c_double)), ("radius", C.c_double)]
+
+
+class FilterC(C.Structure):
+    _fields_ = [("shape", C.c_int32), ("gamma", C.c_double), ("kc", C.c_double), ("p", C.c_double)]
+
+
+class ParamsC(C.Structure):
+    _fields_ = [("lattice", C.c_int32), ("order", C.c_int32), ("nu", C.c_double), ("dt", C.c_double),
+                ("cfl", C.c_double), ("rho0", C.c_double), ("precision", C.c_int32), ("filter", FilterC),
+                ("body_accel", C.c_double * 3)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libselbm.so (raises if it is absent: no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2509_19171_gb300.build`")
+    lib = C.CDLL(path)
+    P, I, D, I64 = C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_int64
+    lib.selbm_create.argtypes = [C.POINTER(MeshC), C.POINTER(ParamsC), P, C.POINTER(P)]
+    lib.selbm_destroy.argtypes = [P]
+    lib.selbm_destroy.restype = None
+    lib.selbm_last_error.argtypes = [P]
+    lib.selbm_last_error.restype = C.c_char_p
+    lib.selbm_info.argtypes = [P, C.POINTER(C.c_int64), D]
+    lib.selbm_lattice_table.argtypes = [P, C.POINTER(C.c_int32), D, C.POINTER(C.c_int32)]
+    lib.selbm_node_coords.argtypes = [P, D]
+    lib.selbm_init.argtypes = [P, P, P, I]
+    lib.selbm_set_state.argtypes = [P, P, I]
+    lib.selbm_get_state.argtypes = [P, P, I]
+    lib.selbm_step.argtypes = [P, I64]
+    lib.selbm_moments.argtypes = [P, P, P, I]
+    lib.selbm_set_filter.argtypes = [P, C.POINTER(FilterC)]
+    lib.selbm_set_body_force.argtypes = [P, D]
+    lib.selbm_diagnostics.argtypes = [P, D]
+    lib.selbm_sync.argtypes = [P]
+    lib.selbm_mesh_check.argtypes = [C.POINTER(MeshC), C.c_int32, C.c_int32, C.POINTER(C.c_int64), D]
+    for name in EXPORTS:
+        if name not in ("selbm_destroy", "selbm_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ptr_of(x):
+    """(pointer, on_device) for a numpy array (host) or a torch tensor (host or CUDA)."""
+    if isinstance(x, np.ndarray):
+        assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"]
+        return C.c_void_p(x.ctypes.data), 0
+    import torch
+    assert isinstance(x, torch.Tensor) and x.dtype == torch.float64 and x.is_contiguous()
+    return C.c_void_p(x.data_ptr()), int(x.is_cuda)
+
+
+def filter_struct(f) -> FilterC:
+    f = f or {}
+    return FilterC(int(f.get("shape", 0)), float(f.get("gamma", 0.0)), float(f.get("kc", 1.0)), float(f.get("p", 8.0)))
+
+
+def mesh_struct(mesh):
+    """(MeshC, keep-alive list) for a workloads.MeshSpec-like object."""
+    dim = int(mesh.dim)
+    keep = [np.ascontiguousarray(mesh.verts, np.float64),
+            np.ascontiguousarray(mesh.curved, np.int32),
+            np.ascontiguousarray(mesh.bc, np.int32),
+            np.ascontiguousarray(mesh.period, np.float64),
+            np.ascontiguousarray(mesh.origin, np.float64),
+            np.ascontiguousarray(np.asarray(mesh.wall_velocity, np.float64).reshape(-1, dim))]
+    v, cu, bc, per, org, wv = keep
+    m = MeshC(dim, int(v.shape[0]), _dptr(v), cu.ctypes.data_as(C.POINTER(C.c_int32)),
+              bc.ctypes.data_as(C.POINTER(C.c_int32)), _dptr(per), _dptr(org), int(wv.shape[0]),
+              _dptr(wv) if wv.size else None, float(getattr(mesh, "radius", 0.0)))
+    return m, keep
+
+
+def mesh_check(mesh, lattice, order):
+    """Host-only dry run of the setup: dict of sizes and integrals (no GPU needed)."""
+    lib = load_library()
+    m, keep = mesh_struct(mesh)
+    ii = (C.c_int64 * 6)()
+    dd = (C.c_double * 4)()
+    lat = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+    rc = lib.selbm_mesh_check(C.byref(m), lat, int(order), ii, dd)
+    if rc != 0:
+        raise SelbmError(rc, lib.selbm_last_error(None).decode())
+    del keep
+    return {"E": ii[0], "Np": ii[1], "Q": ii[2], "G": ii[3], "Gb": ii[4], "affine": bool(ii[5]),
+            "min_spacing": dd[0], "measure": dd[1], "wall_nodes": int(dd[2]), "wall_area": dd[3]}
+
+
+class SELBM:
+    """One simulation handle.  ``mesh`` is a ``workloads.MeshSpec``-like object
+    (dim, verts, curved, bc, period, origin, wall_velocity, radius)."""
+
+    def __init__(self, mesh, lattice, order, nu, cfl=0.5, dt=0.0, rho0=1.0, precision=FP64,
+                 filt=None, body_accel=(0.0, 0.0, 0.0), stream=None):
+        self.lib = load_library()
+        dim = int(mesh.dim)
+        m, self._keep = mesh_struct(mesh)
+        g = list(body_accel) + [0.0] * (3 - len(body_accel))
+        lat = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+        p = ParamsC(lat, int(order), float(nu), float(dt), float(cfl), float(rho0), int(precision),
+                    filter_struct(filt), (C.c_double * 3)(*g[:3]))
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except ImportError:
+                stream = 0
+        self.stream = stream
+        h = C.c_void_p()
+        rc = self.lib.selbm_create(C.byref(m), C.byref(p), C.c_void_p(stream), C.byref(h))
+        if rc != 0:
+            raise SelbmError(rc, self.lib.selbm_last_error(None).decode())
+        self.h = h
+        self.dim = dim
+        self._info()
+
+    def _check(self, rc):
+        if rc != 0:
+            raise SelbmError(rc, self.lib.selbm_last_error(self.h).decode())
+        return rc
+
+    def _info(self):
+        ii = (C.c_int64 * 8)()
+        dd = (C.c_double * 4)()
+        self._check(self.lib.selbm_info(self.h, ii, dd))
+        self.E, self.Np, self.Q, self.G, _, self.N, self.precision, self.steps = [int(x) for x in ii]
+        self.dt, self.tau, self.lam, self.time = [float(x) for x in dd]
+        return self
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.selbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------------- tables
+    def lattice_table(self):
+        e = np.zeros((self.Q, 3), np.int32)
+        t = np.zeros(self.Q)
+        o = np.zeros(self.Q, np.int32)
+        self._check(self.lib.selbm_lattice_table(self.h, e.ctypes.data_as(C.POINTER(C.c_int32)), _dptr(t),
+                                                 o.ctypes.data_as(C.POINTER(C.c_int32))))
+        return e[:, : self.dim], t, o
+
+    def node_coords(self):
+        x = np.zeros((self.E, self.Np, self.dim))
+        self._check(self.lib.selbm_node_coords(self.h, _dptr(x)))
+        return x
+
+    # ------------------------------------------------------------------ state
+    def init(self, rho, u):
+        pr, dev = _ptr_of(rho)
+        pu, _ = _ptr_of(u)
+        self._check(self.lib.selbm_init(self.h, pr, pu, dev))
+
+    def init_from(self, fn):
+        """Evaluate a closed-form initial field fn(x[n, dim]) -> (rho, u) at the nodes."""
+        x = self.node_coords().reshape(-1, self.dim)
+        rho, u = fn(x)
+        self.init(np.ascontiguousarray(rho, np.float64), np.ascontiguousarray(u[:, : self.dim], np.float64))
+
+    def set_state(self, f):
+        pf, dev = _ptr_of(f)
+        self._check(self.lib.selbm_set_state(self.h, pf, dev))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros((self.Q, self.E, self.Np))
+        pf, dev = _ptr_of(out)
+        self._check(self.lib.selbm_get_state(self.h, pf, dev))
+        return out
+
+    def step(self, n=1):
+        self._check(self.lib.selbm_step(self.h, int(n)))
+        self._info()
+
+    def moments(self, rho=None, u=None):
+        if rho is None:
+            rho = np.zeros((self.E, self.Np))
+            u = np.zeros((self.E, self.Np, self.dim))
+        pr, dev = _ptr_of(rho)
+        pu, _ = _ptr_of(u)
+        self._check(self.lib.selbm_moments(self.h, pr, pu, dev))
+        return rho, u
+
+    def set_filter(self, f):
+        fs = filter_struct(f)
+        self._check(self.lib.selbm_set_filter(self.h, C.byref(fs)))
+
+    def set_body_force(self, g):
+        a = np.zeros(3)
+        a[: len(g)] = g
+        self._check(self.lib.selbm_set_body_force(self.h, _dptr(a)))
+
+    def diagnostics(self):
+        out = np.zeros(8)
+        self._check(self.lib.selbm_diagnostics(self.h, _dptr(out)))
+        return out
+
+    def sync(self):
+        self._check(self.lib.selbm_sync(self.h))
+
+
+def from_case(case, precision=FP64, **kw):
+    """Handle for a ``workloads.Case``."""
+    return SELBM(case.mesh, case.lattice, case.order, case.nu, cfl=case.cfl, rho0=case.rho0,
+                 precision=precision, filt=kw.pop("filt", case.filt), body_accel=kw.pop("body_accel", case.body_accel),
+                 **kw)

@@ -1,0 +1,480 @@
+// C ABI of the filtered SELBM library (include/selbm.h): handle creation,
+// upload of the FP64 setup, the step loop, state import/export, diagnostics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/selbm.h"
+#include "selbm_kernels.cuh"
+#include "selbm_setup.h"
+
+using namespace slb;
+
+namespace {
+std::string g_create_error;
+std::once_flag g_const_once;
+
+template <typename T>
+cudaError_t upload(T **dst, const std::vector<T> &src) {
+  *dst = nullptr;
+  if (src.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void **)dst, src.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+template <typename R>
+std::vector<R> cast_vec(const std::vector<double> &v) {
+  return std::vector<R>(v.begin(), v.end());
+}
+}  // namespace
+
+struct selbm {
+  Setup S;
+  selbm_params P{};
+  cudaStream_t stream = nullptr;
+  int lat = 0, Q = 0, prec = 0, rsz = 8;
+  double dt = 0, tau = 0, lam = 0, omega = 0, time = 0;
+  int64_t steps = 0;
+  bool initialized = false, filter_pending = false, filter_on = false, has_force = false;
+  std::string err;
+  std::vector<double> Fmat, sigma;
+  // device buffers (Real = double or float by precision)
+  void *FA = nullptr, *F0 = nullptr, *F2 = nullptr, *T = nullptr, *RHO = nullptr, *BUF = nullptr;
+  void *d_el_drdx = nullptr, *d_el_J = nullptr, *d_drdx = nullptr, *d_wJ = nullptr, *d_gllw = nullptr;
+  void *d_D = nullptr, *d_F = nullptr, *d_wall_u = nullptr, *d_walls = nullptr, *d_minv = nullptr;
+  int32_t *d_l2g = nullptr, *d_bslot = nullptr, *d_bnode_g = nullptr, *d_bnode_off = nullptr, *d_bnode_slot = nullptr;
+  int32_t *d_wall_off = nullptr, *d_first = nullptr;
+  uint8_t *d_owner = nullptr;
+  double *d_mass = nullptr, *d_partial = nullptr, *d_diag = nullptr;
+  double *d_io = nullptr;  // staging for host <-> device FP64 arrays
+  size_t io_bytes = 0;
+  std::vector<void *> allocs;
+
+  int fail(int code, const std::string &m) { err = m; return code; }
+  int cuda_fail(cudaError_t e, const char *where) {
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return SELBM_ERR_CUDA;
+  }
+  size_t nloc() const { return (size_t)S.E * S.Np; }
+};
+
+namespace {
+
+template <typename Real>
+cudaError_t upload_real(selbm *h) {
+  const Setup &S = h->S;
+  cudaError_t e;
+  const size_t G = S.G, Q = h->Q;
+  auto alloc = [&](void **p, size_t bytes) {
+    cudaError_t r = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (r == cudaSuccess) { h->allocs.push_back(*p); cudaMemsetAsync(*p, 0, std::max<size_t>(bytes, 16), h->stream); }
+    return r;
+  };
+  if ((e = alloc(&h->FA, Q * G * sizeof(Real)))) return e;
+  if ((e = alloc(&h->F0, Q * G * sizeof(Real)))) return e;
+  if ((e = alloc(&h->F2, Q * G * sizeof(Real)))) return e;
+  if ((e = alloc(&h->BUF, Q * G * sizeof(Real)))) return e;
+  if ((e = alloc(&h->T, Q * (size_t)S.E * S.Nb * sizeof(Real)))) return e;
+  if ((e = alloc(&h->RHO, G * sizeof(Real)))) return e;
+  Real *p;
+  if (S.affine) {
+    std::vector<double> em = S.el_drdx;
+    // exact zeros for metric entries that vanish up to rounding (axis-aligned elements)
+    const int d = S.dim;
+    for (int el = 0; el < S.E; ++el) {
+      double mx = 0;
+      for (int c = 0; c < d * d; ++c) mx = std::max(mx, std::fabs(em[(size_t)el * d * d + c]));
+      for (int c = 0; c < d * d; ++c)
+        if (std::fabs(em[(size_t)el * d * d + c]) < 1e-13 * mx) em[(size_t)el * d * d + c] = 0.0;
+    }
+    if ((e = upload(&p, cast_vec<Real>(em)))) return e; h->d_el_drdx = p; h->allocs.push_back(p);
+    if ((e = upload(&p, cast_vec<Real>(S.el_J)))) return e; h->d_el_J = p; h->allocs.push_back(p);
+  } else {
+    if ((e = upload(&p, cast_vec<Real>(S.drdx)))) return e; h->d_drdx = p; h->allocs.push_back(p);
+    if ((e = upload(&p, cast_vec<Real>(S.wJ)))) return e; h->d_wJ = p; h->allocs.push_back(p);
+  }
+  if ((e = upload(&p, cast_vec<Real>(S.gll.w)))) return e; h->d_gllw = p; h->allocs.push_back(p);
+  if ((e = upload(&p, cast_vec<Real>(S.gll.D)))) return e; h->d_D = p; h->allocs.push_back(p);
+  if ((e = alloc(&h->d_F, S.n1 * S.n1 * sizeof(Real)))) return e;
+  std::vector<double> wu = S.wall_u;
+  if (wu.empty()) wu.assign(3, 0.0);
+  if ((e = upload(&p, cast_vec<Real>(wu)))) return e; h->d_wall_u = p; h->allocs.push_back(p);
+  std::vector<double> minv(S.Gb);
+  for (int u = 0; u < S.Gb; ++u) minv[u] = 1.0 / S.mass[S.bnode_g[u]];
+  if ((e = upload(&p, cast_vec<Real>(minv)))) return e; h->d_minv = p; h->allocs.push_back(p);
+  // wall nodes grouped per (element, node)
+  std::vector<WallPt<Real>> wp;
+  std::vector<int32_t> woff(S.E + 1, 0);
+  for (int el = 0; el < S.E; ++el) {
+    std::vector<const WallNode *> nodes;
+    for (int k = S.wall_off[el]; k < S.wall_off[el + 1]; ++k) nodes.push_back(&S.walls[k]);
+    std::stable_sort(nodes.begin(), nodes.end(), [](const WallNode *a, const WallNode *b) { return a->i < b->i; });
+    for (size_t k = 0; k < nodes.size();) {
+      WallPt<Real> w{};
+      w.i = nodes[k]->i; w.b = nodes[k]->b; w.nf = 0;
+      while (k < nodes.size() && nodes[k]->i == w.i) {
+        if (w.nf < 3) {
+          for (int c = 0; c < 3; ++c) w.n[w.nf][c] = (Real)nodes[k]->n[c];
+          w.wsJs[w.nf] = (Real)nodes[k]->wsJs;
+          w.wid[w.nf] = nodes[k]->wid;
+          w.nf++;
+        }
+        ++k;
+      }
+      wp.push_back(w);
+    }
+    woff[el + 1] = (int32_t)wp.size();
+  }
+  WallPt<Real> *dw;
+  if ((e = upload(&dw, wp))) return e; h->d_walls = dw; if (dw) h->allocs.push_back(dw);
+  int32_t *q;
+  if ((e = upload(&q, woff))) return e; h->d_wall_off = q; h->allocs.push_back(q);
+  return cudaSuccess;
+}
+
+template <typename Real>
+KParams<Real> base_params(selbm *h) {
+  const Setup &S = h->S;
+  KParams<Real> p{};
+  p.E = S.E; p.Np = S.Np; p.Nb = S.Nb; p.N = S.N; p.n = S.n1; p.G = S.G; p.Gb = S.Gb;
+  p.dt = (Real)h->dt; p.half_dt = (Real)(0.5 * h->dt); p.omega = (Real)h->omega; p.rho0 = (Real)h->P.rho0;
+  for (int k = 0; k < 3; ++k) p.g[k] = (Real)(k < S.dim ? h->P.body_accel[k] : 0.0);
+  p.has_force = h->has_force;
+  p.l2g = h->d_l2g; p.owner = h->d_owner; p.bslot = h->d_bslot;
+  p.el_drdx = (const Real *)h->d_el_drdx; p.el_J = (const Real *)h->d_el_J;
+  p.drdx = (const Real *)h->d_drdx; p.wJ = (const Real *)h->d_wJ; p.gllw = (const Real *)h->d_gllw;
+  p.Dm = (const Real *)h->d_D; p.Fm = (const Real *)h->d_F;
+  p.walls = (const WallPt<Real> *)h->d_walls; p.wall_off = h->d_wall_off; p.wall_u = (const Real *)h->d_wall_u;
+  p.bnode_g = h->d_bnode_g; p.bnode_off = h->d_bnode_off; p.bnode_slot = h->d_bnode_slot;
+  p.bnode_minv = (const Real *)h->d_minv;
+  p.T = (Real *)h->T; p.rho = (Real *)h->RHO;
+  return p;
+}
+
+// one time step: three stages, each = element kernel + assembly kernel
+template <typename Real>
+cudaError_t enqueue_step(selbm *h, bool apply_filter) {
+  KParams<Real> p = base_params<Real>(h);
+  Real *FA = (Real *)h->FA, *F0 = (Real *)h->F0, *F2 = (Real *)h->F2;
+  const Real A[3] = {Real(0), Real(0.75), Real(1.0 / 3.0)};
+  const Real B[3] = {Real(1), Real(0.25), Real(2.0 / 3.0)};
+  const Real *fin[3] = {FA, FA, F2};   // element-kernel input f^{s-1} (stage 1: f^3 of the last step)
+  Real *fout[3] = {FA, F2, FA};
+  cudaError_t e;
+  for (int s = 0; s < 3; ++s) {
+    p.stage = s + 1; p.A = A[s]; p.B = B[s];
+    p.apply_filter = (s == 0 && apply_filter) ? 1 : 0;
+    p.fin = fin[s]; p.f0 = F0; p.fout = fout[s]; p.f0out = F0;
+    if ((e = launch_stage<Real>(h->lat, h->S.affine, p, h->stream))) return e;
+    KParams<Real> q = p;
+    q.fin = (s == 0) ? F0 : fin[s];      // assembly: f^{s-1} on shared nodes (stage 1: f^0)
+    if ((e = launch_dss<Real>(h->lat, q, h->stream))) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename Real>
+cudaError_t enqueue_finalize(selbm *h) {
+  KParams<Real> p = base_params<Real>(h);
+  p.fin = (const Real *)h->FA;
+  p.fout = (Real *)h->BUF;
+  p.apply_filter = (h->filter_pending && h->filter_on) ? 1 : 0;
+  return launch_finalize<Real>(h->lat, p, h->stream);
+}
+
+int set_filter_internal(selbm *h, const selbm_filter &f) {
+  if (f.gamma != 0.0 && !(f.kc >= 1.0 && f.kc < h->S.N)) return h->fail(SELBM_ERR_ARG, "filter kc must satisfy 1 <= kc < N");
+  if (f.gamma < 0.0 || f.gamma > 1.0) return h->fail(SELBM_ERR_ARG, "filter gamma must be in [0, 1]");
+  h->P.filter = f;
+  build_filter(h->S.gll, f, &h->Fmat, &h->sigma);
+  h->filter_on = f.gamma != 0.0;
+  cudaError_t e;
+  if (h->prec == SELBM_FP64)
+    e = cudaMemcpyAsync(h->d_F, h->Fmat.data(), h->Fmat.size() * 8, cudaMemcpyHostToDevice, h->stream);
+  else {
+    std::vector<float> ff(h->Fmat.begin(), h->Fmat.end());
+    e = cudaMemcpyAsync(h->d_F, ff.data(), ff.size() * 4, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "set_filter");
+  return SELBM_OK;
+}
+
+int ensure_io(selbm *h, size_t bytes) {
+  if (h->io_bytes >= bytes) return SELBM_OK;
+  if (h->d_io) cudaFree(h->d_io);
+  h->d_io = nullptr; h->io_bytes = 0;
+  cudaError_t e = cudaMalloc((void **)&h->d_io, bytes);
+  if (e != cudaSuccess) return h->cuda_fail(e, "io buffer");
+  h->io_bytes = bytes;
+  return SELBM_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_stream, selbm_t **out) {
+  if (out) *out = nullptr;
+  if (!mesh || !params || !out) { g_create_error = "NULL argument"; return SELBM_ERR_ARG; }
+  if (params->precision != SELBM_FP64 && params->precision != SELBM_FP32DEV) { g_create_error = "unknown precision"; return SELBM_ERR_ARG; }
+  if (!(params->nu > 0.0)) { g_create_error = "nu must be positive"; return SELBM_ERR_ARG; }
+  selbm *h = new selbm();
+  h->P = *params;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->lat = params->lattice;
+  h->prec = params->precision;
+  h->rsz = h->prec == SELBM_FP64 ? 8 : 4;
+  std::string err;
+  int rc = build_setup(*mesh, params->lattice, params->order, &h->S, &err);
+  if (rc != SELBM_OK) { g_create_error = err; delete h; return rc; }
+  Setup &S = h->S;
+  h->Q = S.lat.Q;
+  const size_t smem = stage_smem_bytes(h->lat, S.Np, S.n1, h->rsz);
+  if (smem > 227 * 1024) { g_create_error = "element tile does not fit in shared memory (use FP32 or a lower order)"; delete h; return SELBM_ERR_ARG; }
+  h->dt = params->dt > 0.0 ? params->dt : params->cfl * S.min_spacing;
+  if (!(h->dt > 0.0)) { g_create_error = "time step must be positive"; delete h; return SELBM_ERR_ARG; }
+  h->lam = params->nu / kCs2;
+  h->tau = h->lam / h->dt;
+  h->omega = 1.0 / (h->tau + 0.5);
+  h->has_force = params->body_accel[0] != 0.0 || params->body_accel[1] != 0.0 || params->body_accel[2] != 0.0;
+  std::call_once(g_const_once, upload_lattice_constants);
+  cudaError_t e = cudaSuccess;
+#define CK(x) do { if ((e = (x)) != cudaSuccess) { g_create_error = std::string(#x) + ": " + cudaGetErrorString(e); selbm_destroy(h); return SELBM_ERR_CUDA; } } while (0)
+  CK(upload(&h->d_l2g, S.l2g));
+  CK(upload(&h->d_owner, S.owner));
+  CK(upload(&h->d_bslot, S.bslot));
+  CK(upload(&h->d_bnode_g, S.bnode_g));
+  CK(upload(&h->d_bnode_off, S.bnode_off));
+  CK(upload(&h->d_bnode_slot, S.bnode_slot));
+  CK(upload(&h->d_first, S.first_copy));
+  CK(upload(&h->d_mass, S.mass));
+  CK(cudaMalloc((void **)&h->d_partial, diag_blocks() * 6 * sizeof(double)));
+  CK(cudaMalloc((void **)&h->d_diag, 8 * sizeof(double)));
+  if (h->prec == SELBM_FP64) CK(upload_real<double>(h)); else CK(upload_real<float>(h));
+#undef CK
+  rc = set_filter_internal(h, params->filter);
+  if (rc != SELBM_OK) { g_create_error = h->err; selbm_destroy(h); return rc; }
+  *out = h;
+  return SELBM_OK;
+}
+
+void selbm_destroy(selbm_t *h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (void *p : h->allocs) cudaFree(p);
+  void *own[] = {h->d_l2g, h->d_owner, h->d_bslot, h->d_bnode_g, h->d_bnode_off, h->d_bnode_slot, h->d_first,
+                 h->d_mass, h->d_partial, h->d_diag, h->d_io};
+  for (void *p : own)
+    if (p) cudaFree(p);
+  delete h;
+}
+
+const char *selbm_last_error(const selbm_t *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int selbm_info(const selbm_t *h, int64_t out_i[8], double out_d[4]) {
+  if (!h) return SELBM_ERR_ARG;
+  if (out_i) {
+    out_i[0] = h->S.E; out_i[1] = h->S.Np; out_i[2] = h->Q; out_i[3] = h->S.G;
+    out_i[4] = h->S.dim; out_i[5] = h->S.N; out_i[6] = h->prec; out_i[7] = h->steps;
+  }
+  if (out_d) { out_d[0] = h->dt; out_d[1] = h->tau; out_d[2] = h->lam; out_d[3] = h->time; }
+  return SELBM_OK;
+}
+
+int selbm_lattice_table(const selbm_t *h, int32_t *e, double *t, int32_t *opp) {
+  if (!h) return SELBM_ERR_ARG;
+  for (int a = 0; a < h->Q; ++a) {
+    if (e) for (int k = 0; k < 3; ++k) e[3 * a + k] = h->S.lat.e[3 * a + k];
+    if (t) t[a] = h->S.lat.t[a];
+    if (opp) opp[a] = h->S.lat.opp[a];
+  }
+  return SELBM_OK;
+}
+
+int selbm_node_coords(const selbm_t *h, double *xyz) {
+  if (!h || !xyz) return SELBM_ERR_ARG;
+  std::memcpy(xyz, h->S.X.data(), h->S.X.size() * sizeof(double));
+  return SELBM_OK;
+}
+
+int selbm_init(selbm_t *h, const double *rho, const double *u, int on_device) {
+  if (!h || !rho || !u) return SELBM_ERR_ARG;
+  const size_t nl = h->nloc(), d = h->S.dim;
+  const double *drho = rho, *du = u;
+  if (!on_device) {
+    int rc = ensure_io(h, nl * (1 + d) * sizeof(double));
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(h->d_io, rho, nl * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_io + nl, u, nl * d * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "init copy");
+    drho = h->d_io; du = h->d_io + nl;
+  }
+  double g[3] = {h->P.body_accel[0], h->P.body_accel[1], h->P.body_accel[2]};
+  cudaError_t e = h->prec == SELBM_FP64
+                      ? launch_init<double>(h->lat, drho, du, h->d_first, h->S.G, h->P.rho0, 0.5 * h->dt, g, h->has_force, (double *)h->FA, h->stream)
+                      : launch_init<float>(h->lat, drho, du, h->d_first, h->S.G, h->P.rho0, 0.5 * h->dt, g, h->has_force, (float *)h->FA, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "init");
+  h->initialized = true; h->filter_pending = false; h->steps = 0; h->time = 0.0;
+  return SELBM_OK;
+}
+
+int selbm_set_state(selbm_t *h, const double *f, int on_device) {
+  if (!h || !f) return SELBM_ERR_ARG;
+  const size_t nl = h->nloc(), bytes = (size_t)h->Q * nl * 8;
+  const double *df = f;
+  if (!on_device) {
+    int rc = ensure_io(h, bytes);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(h->d_io, f, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "set_state copy");
+    df = h->d_io;
+  }
+  cudaError_t e = h->prec == SELBM_FP64
+                      ? launch_set_state<double>(h->lat, df, h->d_first, h->S.G, nl, h->P.rho0, (double *)h->FA, h->stream)
+                      : launch_set_state<float>(h->lat, df, h->d_first, h->S.G, nl, h->P.rho0, (float *)h->FA, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "set_state");
+  h->initialized = true; h->filter_pending = false;
+  return SELBM_OK;
+}
+
+static int finalize(selbm *h) {
+  cudaError_t e = h->prec == SELBM_FP64 ? enqueue_finalize<double>(h) : enqueue_finalize<float>(h);
+  if (e != cudaSuccess) return h->cuda_fail(e, "finalize");
+  return SELBM_OK;
+}
+
+int selbm_get_state(selbm_t *h, double *f, int on_device) {
+  if (!h || !f) return SELBM_ERR_ARG;
+  if (!h->initialized) return h->fail(SELBM_ERR_STATE, "state not initialised");
+  int rc = finalize(h);
+  if (rc) return rc;
+  const size_t nl = h->nloc(), bytes = (size_t)h->Q * nl * 8;
+  double *df = f;
+  if (!on_device) {
+    if ((rc = ensure_io(h, bytes))) return rc;
+    df = h->d_io;
+  }
+  cudaError_t e = h->prec == SELBM_FP64
+                      ? launch_get_state<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, df, h->stream)
+                      : launch_get_state<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, df, h->stream);
+  if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(f, df, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "get_state");
+  return SELBM_OK;
+}
+
+int selbm_step(selbm_t *h, int64_t nsteps) {
+  if (!h) return SELBM_ERR_ARG;
+  if (!h->initialized) return h->fail(SELBM_ERR_STATE, "state not initialised");
+  if (nsteps < 0) return h->fail(SELBM_ERR_ARG, "nsteps < 0");
+  for (int64_t k = 0; k < nsteps; ++k) {
+    const bool filt = h->filter_pending && h->filter_on;
+    cudaError_t e = h->prec == SELBM_FP64 ? enqueue_step<double>(h, filt) : enqueue_step<float>(h, filt);
+    if (e != cudaSuccess) return h->cuda_fail(e, "step");
+    h->filter_pending = true;
+    h->steps++;
+    h->time += h->dt;
+  }
+  return SELBM_OK;
+}
+
+int selbm_moments(selbm_t *h, double *rho, double *u, int on_device) {
+  if (!h || !rho || !u) return SELBM_ERR_ARG;
+  if (!h->initialized) return h->fail(SELBM_ERR_STATE, "state not initialised");
+  int rc = finalize(h);
+  if (rc) return rc;
+  const size_t nl = h->nloc(), d = h->S.dim;
+  double *dr = rho, *du = u;
+  if (!on_device) {
+    if ((rc = ensure_io(h, nl * (1 + d) * 8))) return rc;
+    dr = h->d_io; du = h->d_io + nl;
+  }
+  cudaError_t e = h->prec == SELBM_FP64
+                      ? launch_moments<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, dr, du, h->stream)
+                      : launch_moments<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, dr, du, h->stream);
+  if (e == cudaSuccess && !on_device) {
+    e = cudaMemcpyAsync(rho, dr, nl * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u, du, nl * d * 8, cudaMemcpyDeviceToHost, h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "moments");
+  return SELBM_OK;
+}
+
+int selbm_set_filter(selbm_t *h, const selbm_filter *f) {
+  if (!h || !f) return SELBM_ERR_ARG;
+  if (h->filter_pending && h->filter_on) {
+    // the last step's filter (old settings) must be applied before switching
+    int rc = finalize(h);
+    if (rc) return rc;
+    size_t bytes = (size_t)h->Q * h->S.G * h->rsz;
+    cudaError_t e = cudaMemcpyAsync(h->FA, h->BUF, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "set_filter");
+    h->filter_pending = false;
+  }
+  return set_filter_internal(h, *f);
+}
+
+int selbm_set_body_force(selbm_t *h, const double g[3]) {
+  if (!h || !g) return SELBM_ERR_ARG;
+  for (int k = 0; k < 3; ++k) h->P.body_accel[k] = g[k];
+  h->has_force = g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0;
+  return SELBM_OK;
+}
+
+int selbm_diagnostics(selbm_t *h, double out[8]) {
+  if (!h || !out) return SELBM_ERR_ARG;
+  if (!h->initialized) return h->fail(SELBM_ERR_STATE, "state not initialised");
+  int rc = finalize(h);
+  if (rc) return rc;
+  cudaError_t e = h->prec == SELBM_FP64
+                      ? launch_diag<double>(h->lat, (const double *)h->BUF, h->d_mass, h->S.G, h->P.rho0, h->d_partial, h->d_diag, h->stream)
+                      : launch_diag<float>(h->lat, (const float *)h->BUF, h->d_mass, h->S.G, h->P.rho0, h->d_partial, h->d_diag, h->stream);
+  double tmp[6];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, h->d_diag, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "diagnostics");
+  out[0] = tmp[0];
+  for (int k = 0; k < 3; ++k) out[1 + k] = tmp[1 + k];
+  out[4] = tmp[4]; out[5] = 0.0; out[6] = h->dt; out[7] = h->time;
+  if (tmp[5] > 0) return h->fail(SELBM_ERR_NONFINITE, "state holds non-finite values");
+  return SELBM_OK;
+}
+
+int selbm_mesh_check(const selbm_mesh *mesh, int32_t lattice, int32_t order, int64_t out_i[6], double out_d[4]) {
+  if (!mesh) { g_create_error = "NULL mesh"; return SELBM_ERR_ARG; }
+  Setup S;
+  std::string err;
+  int rc = build_setup(*mesh, lattice, order, &S, &err);
+  if (rc != SELBM_OK) { g_create_error = err; return rc; }
+  if (out_i) {
+    out_i[0] = S.E; out_i[1] = S.Np; out_i[2] = S.lat.Q; out_i[3] = S.G; out_i[4] = S.Gb; out_i[5] = S.affine ? 1 : 0;
+  }
+  if (out_d) {
+    double m = 0.0, ws = 0.0;
+    for (double v : S.mass) m += v;
+    for (const WallNode &w : S.walls) ws += w.wsJs;
+    out_d[0] = S.min_spacing; out_d[1] = m; out_d[2] = (double)S.walls.size(); out_d[3] = ws;
+  }
+  return SELBM_OK;
+}
+
+int selbm_sync(selbm_t *h) {
+  if (!h) return SELBM_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "sync");
+  return SELBM_OK;
+}
+
+}  // extern "C"

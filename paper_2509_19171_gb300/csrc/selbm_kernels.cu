@@ -1,0 +1,541 @@
+// Hot-path kernels of the filtered SELBM (paper Sec. 2): per-stage element
+// kernel (optional filter + BGK collision in stage 1, tensor-product GLL
+// derivative with metrics, flux bounce-back, Runge-Kutta combination at
+// element-interior nodes, weighted contributions of element-boundary nodes),
+// and the assembly kernel that finishes the shared nodes.
+#include <cstdio>
+
+#include "selbm_kernels.cuh"
+#include "selbm_setup.h"
+
+namespace slb {
+
+template <int LAT> struct Lat;
+template <> struct Lat<SELBM_D2Q9> { static constexpr int Q = 9, D = 2; };
+template <> struct Lat<SELBM_D3Q19> { static constexpr int Q = 19, D = 3; };
+template <> struct Lat<SELBM_D3Q27> { static constexpr int Q = 27, D = 3; };
+
+__constant__ int8_t c_e[3][kMaxQ][3];
+__constant__ double c_td[3][kMaxQ];
+__constant__ float c_tf[3][kMaxQ];
+__constant__ int8_t c_opp[3][kMaxQ];
+
+void upload_lattice_constants() {
+  int8_t e[3][kMaxQ][3] = {};
+  double td[3][kMaxQ] = {};
+  float tf[3][kMaxQ] = {};
+  int8_t opp[3][kMaxQ] = {};
+  for (int l = 0; l < 3; ++l) {
+    Lattice L;
+    build_lattice(l, &L);
+    for (int a = 0; a < L.Q; ++a) {
+      for (int k = 0; k < 3; ++k) e[l][a][k] = (int8_t)L.e[3 * a + k];
+      td[l][a] = L.t[a];
+      tf[l][a] = (float)L.t[a];
+      opp[l][a] = (int8_t)L.opp[a];
+    }
+  }
+  cudaMemcpyToSymbol(c_e, e, sizeof(e));
+  cudaMemcpyToSymbol(c_td, td, sizeof(td));
+  cudaMemcpyToSymbol(c_tf, tf, sizeof(tf));
+  cudaMemcpyToSymbol(c_opp, opp, sizeof(opp));
+}
+
+template <typename Real> __device__ __forceinline__ Real wt(int lat, int a);
+template <> __device__ __forceinline__ double wt<double>(int lat, int a) { return c_td[lat][a]; }
+template <> __device__ __forceinline__ float wt<float>(int lat, int a) { return c_tf[lat][a]; }
+
+constexpr int kMaxN1 = kMaxN + 1;
+
+size_t stage_smem_bytes(int lat, int Np, int n, int real_size) {
+  const int Q = lat == SELBM_D2Q9 ? 9 : (lat == SELBM_D3Q19 ? 19 : 27);
+  return (size_t)(Q * Np + 2 * n * n + Np) * real_size;
+}
+
+// ---------------------------------------------------------------------------
+// element-tile helpers (tile sf[Q][Np] in shared memory, r index fastest)
+// ---------------------------------------------------------------------------
+
+// base index and stride of the line through line-number L along `axis`
+__device__ __forceinline__ void line_base(int axis, int L, int n, int *base, int *stride) {
+  if (axis == 0) { *base = L * n; *stride = 1; }
+  else if (axis == 1) { *base = (L % n) + n * n * (L / n); *stride = n; }
+  else { *base = L; *stride = n * n; }
+}
+
+// one 1D filter pass along `axis` for every population (lines are disjoint)
+template <typename Real, int Q>
+__device__ void filter_pass(Real *sf, const Real *sF, int n, int Np, int axis) {
+  const int nl = Np / n;
+  for (int idx = threadIdx.x; idx < Q * nl; idx += blockDim.x) {
+    const int a = idx / nl, L = idx - a * nl;
+    int base, stride;
+    line_base(axis, L, n, &base, &stride);
+    Real *row = sf + a * Np + base;
+    Real v[kMaxN1];
+#pragma unroll
+    for (int k = 0; k < kMaxN1; ++k)
+      if (k < n) v[k] = row[k * stride];
+    for (int m = 0; m < n; ++m) {
+      Real s = 0;
+#pragma unroll
+      for (int k = 0; k < kMaxN1; ++k)
+        if (k < n) s += sF[m * n + k] * v[k];
+      row[m * stride] = s;
+    }
+  }
+}
+
+// BGK collision with the higher-order force at local node i (deviation form:
+// the tile holds g = f_bar - t rho0).  Sec. 2.1:
+//   f_bar^eq = f^eq - dt/2 F**,  f* = f_bar - omega (f_bar - f_bar^eq) + dt F**,  omega = 1/(tau + 1/2)
+template <typename Real, int LAT>
+__device__ void collide_node(Real *sf, int i, const KParams<Real> &p, Real *srho, int e) {
+  constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
+  const int Np = p.Np;
+  Real drho = 0, j[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const Real v = sf[a * Np + i];
+    drho += v;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) j[k] += (Real)c_e[LAT][a][k] * v;
+  }
+  const Real rho = p.rho0 + drho;
+  const Real inv = Real(1) / rho;
+  Real u[3] = {0, 0, 0}, F[3] = {0, 0, 0};
+  Real uu = 0, uF = 0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    u[k] = j[k] * inv;
+    uu += u[k] * u[k];
+    if (p.has_force) { F[k] = rho * p.g[k]; uF += u[k] * F[k]; }
+  }
+  const Real ics2 = Real(3), ics4 = Real(9);
+  const size_t gid = p.l2g[(size_t)e * Np + i];
+  const bool own = p.owner[(size_t)e * Np + i] != 0;
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    Real eu = 0, eF = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { eu += (Real)c_e[LAT][a][k] * u[k]; eF += (Real)c_e[LAT][a][k] * F[k]; }
+    const Real t = wt<Real>(LAT, a);
+    Real feq = t * (drho + rho * (eu * ics2 + Real(0.5) * eu * eu * ics4 - Real(0.5) * uu * ics2));
+    Real Fss = 0;
+    if (p.has_force) {
+      Fss = t * (eu * eF * ics4 - uF * ics2);
+      feq -= p.half_dt * Fss;
+    }
+    const Real v = sf[a * Np + i];
+    const Real out = v - p.omega * (v - feq) + p.dt * Fss;
+    sf[a * Np + i] = out;
+    if (own) p.f0out[a * (size_t)p.G + gid] = out;
+  }
+  srho[i] = rho;
+  if (own && p.has_force) p.rho[gid] = rho;
+}
+
+// ---------------------------------------------------------------------------
+// stage kernel: one CTA per element
+// ---------------------------------------------------------------------------
+template <typename Real, int LAT, bool AFFINE>
+__global__ void __launch_bounds__(512) stage_kernel(const KParams<Real> p) {
+  constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, Np = p.Np;
+  Real *sf = reinterpret_cast<Real *>(smem_raw);
+  Real *sD = sf + Q * Np;
+  Real *sF = sD + n * n;
+  Real *srho = sF + n * n;
+  const int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  for (int k = tid; k < n * n; k += nt) { sD[k] = p.Dm[k]; sF[k] = p.Fm[k]; }
+  const int32_t *l2g = p.l2g + (size_t)e * Np;
+  for (int idx = tid; idx < Q * Np; idx += nt) {
+    const int a = idx / Np, i = idx - a * Np;
+    sf[idx] = p.fin[(size_t)a * p.G + l2g[i]];
+  }
+  __syncthreads();
+  if (p.stage == 1) {
+    if (p.apply_filter) {
+      for (int axis = 0; axis < DIM; ++axis) {
+        filter_pass<Real, Q>(sf, sF, n, Np, axis);
+        __syncthreads();
+      }
+    }
+    for (int i = tid; i < Np; i += nt) collide_node<Real, LAT>(sf, i, p, srho, e);
+    __syncthreads();
+  }
+
+  // metric coefficients of the element (affine case)
+  Real em[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  Real Je = 0;
+  if (AFFINE) {
+#pragma unroll
+    for (int l = 0; l < DIM; ++l)
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) em[l][k] = p.el_drdx[((size_t)e * DIM + l) * DIM + k];
+    Je = p.el_J[e];
+  }
+  const Real ics2 = Real(3);
+  const size_t EN = (size_t)p.E * p.Nb;
+  for (int idx = tid; idx < Q * Np; idx += nt) {
+    const int a = idx / Np, i = idx - a * Np;
+    int ii[3] = {i % n, (i / n) % n, DIM == 3 ? i / (n * n) : 0};
+    const int strides[3] = {1, n, n * n};
+    // e_alpha . grad f = sum_l (sum_k e_k dr_l/dx_k) (D_l f)   (chain rule, Sec. 2.2)
+    Real adv = 0;
+#pragma unroll
+    for (int l = 0; l < DIM; ++l) {
+      Real coef = 0;
+      if (AFFINE) {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) coef += (Real)c_e[LAT][a][k] * em[l][k];
+      } else {
+        const Real *gm = p.drdx + (((size_t)e * Np + i) * DIM + l) * DIM;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) coef += (Real)c_e[LAT][a][k] * gm[k];
+      }
+      if (coef != Real(0)) {
+        const Real *row = sf + a * Np + (i - ii[l] * strides[l]);
+        const Real *drow = sD + ii[l] * n;
+        Real d = 0;
+#pragma unroll
+        for (int k = 0; k < kMaxN1; ++k)
+          if (k < n) d += drow[k] * row[k * strides[l]];
+        adv += coef * d;
+      }
+    }
+    const int b = p.bslot[i];
+    const size_t gid = l2g[i];
+    if (b < 0) {
+      Real Fs = 0;
+      if (p.has_force) {
+        const Real rho_i = p.stage == 1 ? srho[i] : p.rho[gid];
+        Real eg = 0;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) eg += (Real)c_e[LAT][a][k] * p.g[k];
+        Fs = wt<Real>(LAT, a) * eg * rho_i * ics2;
+      }
+      const Real fprev = sf[idx];
+      const Real f0v = p.stage == 1 ? fprev : p.f0[(size_t)a * p.G + gid];
+      p.fout[(size_t)a * p.G + gid] = p.A * f0v + p.B * (fprev + p.dt * (Fs - adv));
+    } else {
+      Real wJi;
+      if (AFFINE) {
+        wJi = Je * p.gllw[ii[0]] * p.gllw[ii[1]];
+        if (DIM == 3) wJi *= p.gllw[ii[2]];
+      } else {
+        wJi = p.wJ[(size_t)e * Np + i];
+      }
+      p.T[a * EN + (size_t)e * p.Nb + b] = -wJi * adv;
+    }
+  }
+  // flux bounce-back on the element's wall nodes (Sec. 2.2.1):
+  //   + w_s J_s (n.e_a) [f_a - f_opp(a) - 2 t_a rho0 (e_a.u_b)/cs2]  for n.e_a < 0
+  const int w0 = p.wall_off[e], w1 = p.wall_off[e + 1];
+  if (w1 > w0) {
+    __syncthreads();
+    for (int idx = tid; idx < Q * (w1 - w0); idx += nt) {
+      const int a = idx % Q;
+      const WallPt<Real> &wp = p.walls[w0 + idx / Q];
+      const int oa = c_opp[LAT][a];
+      Real sum = 0;
+      for (int f = 0; f < wp.nf; ++f) {
+        Real ne = 0, eu = 0;
+        const Real *ub = p.wall_u + 3 * (wp.wid[f] - 1);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+          ne += wp.n[f][k] * (Real)c_e[LAT][a][k];
+          eu += (Real)c_e[LAT][a][k] * ub[k];
+        }
+        if (ne < Real(0)) {
+          const Real jump = sf[a * Np + wp.i] - sf[oa * Np + wp.i] - Real(2) * wt<Real>(LAT, a) * p.rho0 * eu * ics2;
+          sum += wp.wsJs[f] * ne * jump;
+        }
+      }
+      p.T[a * EN + (size_t)e * p.Nb + wp.b] += sum;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// assembly of element-boundary nodes: f^s = A f^0 + B (f^{s-1} + dt (sum_c T_c / M + F*))
+// copies summed in ascending (element, local node) order
+// ---------------------------------------------------------------------------
+template <typename Real, int LAT>
+__global__ void dss_kernel(const KParams<Real> p) {
+  constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
+  const size_t total = (size_t)Q * p.Gb;
+  const size_t EN = (size_t)p.E * p.Nb;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / p.Gb), u = (int)(idx - (size_t)a * p.Gb);
+    Real s = 0;
+    const Real *Ta = p.T + a * EN;
+    for (int c = p.bnode_off[u]; c < p.bnode_off[u + 1]; ++c) s += Ta[p.bnode_slot[c]];
+    const size_t gid = p.bnode_g[u];
+    Real Fs = 0;
+    if (p.has_force) {
+      Real eg = 0;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) eg += (Real)c_e[LAT][a][k] * p.g[k];
+      Fs = wt<Real>(LAT, a) * eg * p.rho[gid] * Real(3);
+    }
+    const Real fprev = p.fin[(size_t)a * p.G + gid];
+    const Real f0v = p.f0[(size_t)a * p.G + gid];
+    p.fout[(size_t)a * p.G + gid] = p.A * f0v + p.B * (fprev + p.dt * (s * p.bnode_minv[u] + Fs));
+  }
+}
+
+// filtered copy (owners write) used to read the state back between steps
+template <typename Real, int LAT>
+__global__ void __launch_bounds__(512) finalize_kernel(const KParams<Real> p) {
+  constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, Np = p.Np;
+  Real *sf = reinterpret_cast<Real *>(smem_raw);
+  Real *sF = sf + Q * Np + n * n;
+  const int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  for (int k = tid; k < n * n; k += nt) sF[k] = p.Fm[k];
+  const int32_t *l2g = p.l2g + (size_t)e * Np;
+  for (int idx = tid; idx < Q * Np; idx += nt) {
+    const int a = idx / Np, i = idx - a * Np;
+    sf[idx] = p.fin[(size_t)a * p.G + l2g[i]];
+  }
+  __syncthreads();
+  if (p.apply_filter) {
+    for (int axis = 0; axis < DIM; ++axis) {
+      filter_pass<Real, Q>(sf, sF, n, Np, axis);
+      __syncthreads();
+    }
+  }
+  for (int idx = tid; idx < Q * Np; idx += nt) {
+    const int a = idx / Np, i = idx - a * Np;
+    if (p.owner[(size_t)e * Np + i]) p.fout[(size_t)a * p.G + l2g[i]] = sf[idx];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int block_for(int lat) { return lat == SELBM_D2Q9 ? 256 : 512; }
+
+template <typename Real, int LAT, bool AFF>
+static cudaError_t launch_stage_t(const KParams<Real> &p, cudaStream_t s) {
+  const size_t smem = stage_smem_bytes(LAT, p.Np, p.n, sizeof(Real));
+  auto k = stage_kernel<Real, LAT, AFF>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k<<<p.E, block_for(LAT), smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_stage(int lat, bool affine, const KParams<Real> &p, cudaStream_t s) {
+  switch (lat) {
+    case SELBM_D2Q9: return affine ? launch_stage_t<Real, SELBM_D2Q9, true>(p, s) : launch_stage_t<Real, SELBM_D2Q9, false>(p, s);
+    case SELBM_D3Q19: return affine ? launch_stage_t<Real, SELBM_D3Q19, true>(p, s) : launch_stage_t<Real, SELBM_D3Q19, false>(p, s);
+    case SELBM_D3Q27: return affine ? launch_stage_t<Real, SELBM_D3Q27, true>(p, s) : launch_stage_t<Real, SELBM_D3Q27, false>(p, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename Real, int LAT>
+static cudaError_t launch_dss_t(const KParams<Real> &p, cudaStream_t s) {
+  const size_t total = (size_t)Lat<LAT>::Q * p.Gb;
+  if (total == 0) return cudaSuccess;
+  const int threads = 256;
+  const int blocks = (int)std::min<size_t>((total + threads - 1) / threads, 152 * 32);
+  dss_kernel<Real, LAT><<<blocks, threads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_dss(int lat, const KParams<Real> &p, cudaStream_t s) {
+  switch (lat) {
+    case SELBM_D2Q9: return launch_dss_t<Real, SELBM_D2Q9>(p, s);
+    case SELBM_D3Q19: return launch_dss_t<Real, SELBM_D3Q19>(p, s);
+    case SELBM_D3Q27: return launch_dss_t<Real, SELBM_D3Q27>(p, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename Real, int LAT>
+static cudaError_t launch_finalize_t(const KParams<Real> &p, cudaStream_t s) {
+  const size_t smem = stage_smem_bytes(LAT, p.Np, p.n, sizeof(Real));
+  auto k = finalize_kernel<Real, LAT>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k<<<p.E, block_for(LAT), smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_finalize(int lat, const KParams<Real> &p, cudaStream_t s) {
+  switch (lat) {
+    case SELBM_D2Q9: return launch_finalize_t<Real, SELBM_D2Q9>(p, s);
+    case SELBM_D3Q19: return launch_finalize_t<Real, SELBM_D3Q19>(p, s);
+    case SELBM_D3Q27: return launch_finalize_t<Real, SELBM_D3Q27>(p, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// state import / export and diagnostics
+// ---------------------------------------------------------------------------
+
+// f_bar = f^eq(rho, u) - dt/2 F** stored as g = f_bar - t rho0 (Sec. 2.1, f at equilibrium)
+template <typename Real, int LAT>
+__global__ void init_kernel(const double *rho, const double *u, const int32_t *first, int G, double rho0,
+                            double half_dt, double gx, double gy, double gz, int has_force, Real *out) {
+  constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    const size_t q = first[g];
+    const double r = rho[q];
+    double uv[3] = {0, 0, 0}, F[3] = {0, 0, 0}, gg[3] = {gx, gy, gz};
+    double uu = 0, uF = 0;
+    for (int k = 0; k < DIM; ++k) {
+      uv[k] = u[q * DIM + k];
+      uu += uv[k] * uv[k];
+      F[k] = has_force ? r * gg[k] : 0.0;
+      uF += uv[k] * F[k];
+    }
+    for (int a = 0; a < Q; ++a) {
+      double eu = 0, eF = 0;
+      for (int k = 0; k < DIM; ++k) { eu += c_e[LAT][a][k] * uv[k]; eF += c_e[LAT][a][k] * F[k]; }
+      const double t = c_td[LAT][a];
+      const double feq = t * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+      const double Fss = t * (9.0 * eu * eF - 3.0 * uF);
+      out[(size_t)a * G + g] = (Real)(feq - half_dt * Fss - t * rho0);
+    }
+  }
+}
+
+template <typename Real, int LAT>
+__global__ void set_state_kernel(const double *f, const int32_t *first, int G, size_t nloc, double rho0, Real *out) {
+  constexpr int Q = Lat<LAT>::Q;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+    for (int a = 0; a < Q; ++a) out[(size_t)a * G + g] = (Real)(f[(size_t)a * nloc + first[g]] - c_td[LAT][a] * rho0);
+}
+
+template <typename Real, int LAT>
+__global__ void get_state_kernel(const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double *f) {
+  constexpr int Q = Lat<LAT>::Q;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nloc; q += (size_t)gridDim.x * blockDim.x)
+    for (int a = 0; a < Q; ++a) f[(size_t)a * nloc + q] = (double)buf[(size_t)a * G + l2g[q]] + c_td[LAT][a] * rho0;
+}
+
+// rho = sum f_bar, rho u = sum e f_bar at every local node (FP64 sums)
+template <typename Real, int LAT>
+__global__ void moments_kernel(const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double *rho, double *u) {
+  constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nloc; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t g = l2g[q];
+    double d = 0, j[3] = {0, 0, 0};
+    for (int a = 0; a < Q; ++a) {
+      const double v = (double)buf[(size_t)a * G + g];
+      d += v;
+      for (int k = 0; k < DIM; ++k) j[k] += c_e[LAT][a][k] * v;
+    }
+    const double r = rho0 + d;
+    rho[q] = r;
+    for (int k = 0; k < DIM; ++k) u[q * DIM + k] = j[k] / r;
+  }
+}
+
+// per-block partial sums: mass, momentum[3], KE, non-finite count (deterministic two-pass)
+template <typename Real, int LAT>
+__global__ void diag_partial_kernel(const Real *buf, const double *mass, int G, double rho0, double *partial) {
+  constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
+  __shared__ double red[6][256];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    double d = 0, j[3] = {0, 0, 0};
+    for (int a = 0; a < Q; ++a) {
+      const double v = (double)buf[(size_t)a * G + g];
+      if (!isfinite(v)) acc[5] += 1.0;
+      d += v;
+      for (int k = 0; k < DIM; ++k) j[k] += c_e[LAT][a][k] * v;
+    }
+    const double r = rho0 + d, M = mass[g];
+    acc[0] += M * r;
+    double uu = 0;
+    for (int k = 0; k < DIM; ++k) { acc[1 + k] += M * j[k]; uu += (j[k] / r) * (j[k] / r); }
+    acc[4] += 0.5 * rho0 * M * uu;
+  }
+  for (int c = 0; c < 6; ++c) red[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int c = 0; c < 6; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 6; ++c) partial[blockIdx.x * 6 + c] = red[c][0];
+}
+
+__global__ void diag_final_kernel(const double *partial, int nblocks, double *out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nblocks; ++b)
+      for (int c = 0; c < 6; ++c) acc[c] += partial[b * 6 + c];
+    for (int c = 0; c < 6; ++c) out[c] = acc[c];
+  }
+}
+
+static int grid_for(size_t n, int threads) { return (int)std::min<size_t>((n + threads - 1) / threads, 152 * 16); }
+
+#define SELBM_LAT_SWITCH(lat, CALL)                  \
+  switch (lat) {                                     \
+    case SELBM_D2Q9: { constexpr int L = SELBM_D2Q9; CALL; } break;  \
+    case SELBM_D3Q19: { constexpr int L = SELBM_D3Q19; CALL; } break; \
+    case SELBM_D3Q27: { constexpr int L = SELBM_D3Q27; CALL; } break; \
+    default: return cudaErrorInvalidValue;           \
+  }
+
+template <typename Real>
+cudaError_t launch_init(int lat, const double *rho, const double *u, const int32_t *first, int G, double rho0,
+                        double half_dt, const double g[3], int has_force, Real *out, cudaStream_t s) {
+  SELBM_LAT_SWITCH(lat, (init_kernel<Real, L><<<grid_for(G, 256), 256, 0, s>>>(rho, u, first, G, rho0, half_dt, g[0], g[1], g[2], has_force, out)));
+  return cudaGetLastError();
+}
+template <typename Real>
+cudaError_t launch_set_state(int lat, const double *f, const int32_t *first, int G, size_t nloc, double rho0, Real *out, cudaStream_t s) {
+  SELBM_LAT_SWITCH(lat, (set_state_kernel<Real, L><<<grid_for(G, 256), 256, 0, s>>>(f, first, G, nloc, rho0, out)));
+  return cudaGetLastError();
+}
+template <typename Real>
+cudaError_t launch_get_state(int lat, const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double *f, cudaStream_t s) {
+  SELBM_LAT_SWITCH(lat, (get_state_kernel<Real, L><<<grid_for(nloc, 256), 256, 0, s>>>(buf, l2g, G, nloc, rho0, f)));
+  return cudaGetLastError();
+}
+template <typename Real>
+cudaError_t launch_moments(int lat, const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double *rho, double *u, cudaStream_t s) {
+  SELBM_LAT_SWITCH(lat, (moments_kernel<Real, L><<<grid_for(nloc, 256), 256, 0, s>>>(buf, l2g, G, nloc, rho0, rho, u)));
+  return cudaGetLastError();
+}
+int diag_blocks() { return 152 * 4; }
+template <typename Real>
+cudaError_t launch_diag(int lat, const Real *buf, const double *mass, int G, double rho0, double *partial, double *out, cudaStream_t s) {
+  SELBM_LAT_SWITCH(lat, (diag_partial_kernel<Real, L><<<diag_blocks(), 256, 0, s>>>(buf, mass, G, rho0, partial)));
+  diag_final_kernel<<<1, 32, 0, s>>>(partial, diag_blocks(), out);
+  return cudaGetLastError();
+}
+
+#define SELBM_INST_UTIL(Real)                                                                                              \
+  template cudaError_t launch_init<Real>(int, const double *, const double *, const int32_t *, int, double, double,      \
+                                         const double[3], int, Real *, cudaStream_t);                                    \
+  template cudaError_t launch_set_state<Real>(int, const double *, const int32_t *, int, size_t, double, Real *, cudaStream_t); \
+  template cudaError_t launch_get_state<Real>(int, const Real *, const int32_t *, int, size_t, double, double *, cudaStream_t); \
+  template cudaError_t launch_moments<Real>(int, const Real *, const int32_t *, int, size_t, double, double *, double *, cudaStream_t); \
+  template cudaError_t launch_diag<Real>(int, const Real *, const double *, int, double, double *, double *, cudaStream_t);
+SELBM_INST_UTIL(double)
+SELBM_INST_UTIL(float)
+
+template cudaError_t launch_stage<double>(int, bool, const KParams<double> &, cudaStream_t);
+template cudaError_t launch_stage<float>(int, bool, const KParams<float> &, cudaStream_t);
+template cudaError_t launch_dss<double>(int, const KParams<double> &, cudaStream_t);
+template cudaError_t launch_dss<float>(int, const KParams<float> &, cudaStream_t);
+template cudaError_t launch_finalize<double>(int, const KParams<double> &, cudaStream_t);
+template cudaError_t launch_finalize<float>(int, const KParams<float> &, cudaStream_t);
+
+}  // namespace slb

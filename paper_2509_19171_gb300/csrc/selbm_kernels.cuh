@@ -1,0 +1,72 @@
+// Device-side data structures and launch helpers of the filtered SELBM hot path.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace slb {
+
+// One element-local wall node: up to three wall faces meet at a node of a hex.
+template <typename Real>
+struct WallPt {
+  int32_t i, b, nf, wid[3];
+  Real n[3][3];
+  Real wsJs[3];
+};
+
+// Everything a stage / assembly / utility kernel reads.  Passed by value.
+template <typename Real>
+struct KParams {
+  int E, Np, Nb, N, n, G, Gb;
+  int stage;                 // 1, 2, 3
+  Real A, B;                 // f^s = A f^0 + B (f^{s-1} + dt L(f^{s-1}))
+  Real dt, omega, rho0, half_dt;
+  Real g[3];
+  int has_force, apply_filter;
+  const int32_t *l2g;        // [E][Np]
+  const uint8_t *owner;      // [E][Np]
+  const int32_t *bslot;      // [Np]
+  const Real *el_drdx;       // [E][dim][dim] affine metrics
+  const Real *el_J;          // [E]
+  const Real *drdx;          // [E][Np][dim][dim] general metrics
+  const Real *wJ;            // [E][Np]
+  const Real *gllw;          // [n]
+  const Real *Dm, *Fm;       // [n][n]
+  const WallPt<Real> *walls; // element-grouped wall nodes
+  const int32_t *wall_off;   // [E+1]
+  const Real *wall_u;        // [nwalls][3]
+  const int32_t *bnode_g, *bnode_off, *bnode_slot;
+  const Real *bnode_minv;    // [Gb] 1 / assembled mass
+  const Real *fin;           // f^{s-1} on unique nodes [Q][G]
+  const Real *f0;            // f^0 [Q][G]
+  Real *fout;                // f^s [Q][G]
+  Real *f0out;               // stage 1: f^0 written by owners
+  Real *T;                   // assembly trace [Q][E*Nb]
+  Real *rho;                 // [G] density of the step (forcing)
+};
+
+// Launchers (defined in selbm_kernels.cu).  lat = SELBM_D2Q9 / D3Q19 / D3Q27.
+template <typename Real>
+cudaError_t launch_stage(int lat, bool affine, const KParams<Real> &p, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_dss(int lat, const KParams<Real> &p, cudaStream_t s);
+// filtered copy of fin into fout on unique nodes (owners write)
+template <typename Real>
+cudaError_t launch_finalize(int lat, const KParams<Real> &p, cudaStream_t s);
+
+template <typename Real>
+cudaError_t launch_init(int lat, const double *rho, const double *u, const int32_t *first, int G, double rho0,
+                        double half_dt, const double g[3], int has_force, Real *out, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_set_state(int lat, const double *f, const int32_t *first, int G, size_t nloc, double rho0, Real *out, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_get_state(int lat, const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double *f, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_moments(int lat, const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double *rho, double *u, cudaStream_t s);
+int diag_blocks();
+template <typename Real>
+cudaError_t launch_diag(int lat, const Real *buf, const double *mass, int G, double rho0, double *partial, double *out, cudaStream_t s);
+
+void upload_lattice_constants();
+size_t stage_smem_bytes(int lat, int Np, int n, int real_size);
+
+}  // namespace slb

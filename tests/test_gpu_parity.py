@@ -1,0 +1,187 @@
+"""GPU (CUDA, sm_103a) parity against the FP64 oracle, through the C ABI.
+
+Tolerances: FP64 path <= 1e-12 relative max-norm on the state after one step
+and <= 1e-9 on rho and u after 1000 steps; FP32-deviation path within the
+FP32 bound stated in each test.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.selbm import OracleSELBM
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_19171_gb300 import build
+    build.build()
+    import paper_2509_19171_gb300 as pkg
+    return pkg
+
+
+def pair(P, mesh, lat, N, nu, precision=0, filt=None, g=(0.0, 0.0, 0.0), cfl=0.5, init=None):
+    o = OracleSELBM(mesh, lat, N, nu, cfl=cfl, filt=filt, body_accel=g)
+    s = P.SELBM(mesh, lat, N, nu, cfl=cfl, precision=precision, filt=filt, body_accel=g)
+    assert abs(s.dt - o.dt) < 1e-15 and s.G == o.G
+    e, t, _ = s.lattice_table()
+    assert np.array_equal(e, o.e) and np.allclose(t, o.t, rtol=0, atol=1e-17)
+    if init is not None:
+        f = o.initial_state_from(init)
+        s.init_from(init)
+    return o, s
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def random_continuous_state(o, amp, seed):
+    """Equilibrium at random (rho, u) plus a random non-equilibrium part, on unique nodes."""
+    rng = np.random.default_rng(seed)
+    rho = 1 + 0.01 * rng.standard_normal(o.G)
+    u = amp * rng.standard_normal((o.G, o.dim))
+    f = o.initial_state(rho, u)
+    return f + 1e-3 * o.t[:, None] * rng.standard_normal((o.Q, o.G))
+
+
+def check_one_step(P, o, s, f, tol):
+    s.set_state(np.ascontiguousarray(o.to_local(f)))
+    s.step(1)
+    fo = o.step(f)
+    fg = s.get_state()
+    err = rel(fg, o.to_local(fo))
+    assert err <= tol, err
+    return fo
+
+
+def test_couette_one_step_and_1000(P):
+    c = W.couette_case()
+    o, s = pair(P, c.mesh, c.lattice, c.order, c.nu, filt=c.filt, init=c.init)
+    f = o.initial_state_from(c.init)
+    f = o.step(f)
+    s.step(1)
+    assert rel(s.get_state(), o.to_local(f)) <= 1e-12
+    f = o.run(f, 999)
+    s.step(999)
+    rho_o, u_o = o.moments(f)
+    rho_g, u_g = s.moments()
+    assert float(np.abs(rho_g - rho_o[o.glo]).max() / np.abs(rho_o).max()) <= 1e-9
+    assert float(np.abs(u_g - u_o[o.glo]).max()) <= 1e-9 * c.U0
+
+
+def test_shear_layer_filtered_random_state(P):
+    """Periodic D2Q9, N=8, exponential filter (double shear layer geometry, 5x3 ragged)."""
+    mesh = W.box_mesh((5, 3), (0, 0), (1, 1), (True, True))
+    filt = {"shape": 1, "gamma": 0.1, "kc": 6.0, "p": 8.0}
+    o, s = pair(P, mesh, "D2Q9", 8, 4e-6 * 100, filt=filt)
+    f = random_continuous_state(o, 0.04, 1)
+    f = check_one_step(P, o, s, f, 1e-12)
+    # the filter of the last step is applied before the next collision: second step
+    fo = o.step(f)
+    s.step(1)
+    assert rel(s.get_state(), o.to_local(fo)) <= 1e-12
+
+
+def test_shear_layer_100_steps(P):
+    mesh = W.box_mesh((4, 4), (0, 0), (1, 1), (True, True))
+    case = W.shear_layer_case(n=4, order=8)
+    o, s = pair(P, mesh, "D2Q9", 8, case.nu, filt=case.filt, init=case.init)
+    f = o.run(o.initial_state_from(case.init), 100)
+    s.step(100)
+    rho_o, u_o = o.moments(f)
+    rho_g, u_g = s.moments()
+    assert float(np.abs(rho_g - rho_o[o.glo]).max()) <= 1e-9
+    assert float(np.abs(u_g - u_o[o.glo]).max()) <= 1e-9 * case.U0
+    d = s.diagnostics()
+    m, mom, ke = o.integrals(f)
+    assert abs(d[0] - m) <= 1e-12 * m and abs(d[4] - ke) <= 1e-9 * ke
+
+
+@pytest.mark.parametrize("lat", ["D3Q19", "D3Q27"])
+def test_tgv3d_box_quadratic_filter(P, lat):
+    L = 2 * math.pi
+    mesh = W.box_mesh((3, 2, 2), (0, 0, 0), (L, L, L), (True, True, True))
+    filt = {"shape": 0, "gamma": 0.1, "kc": 3.0}
+    init = W.tgv3d_init(0.05)
+    o, s = pair(P, mesh, lat, 5, 0.05 / 1600, filt=filt, init=init)
+    f = o.initial_state_from(init)
+    f = o.step(f)
+    s.step(1)
+    assert rel(s.get_state(), o.to_local(f)) <= 1e-12
+    f = o.run(f, 9)
+    s.step(9)
+    assert rel(s.get_state(), o.to_local(f)) <= 1e-11
+
+
+def test_pipe_curved_walls_force(P):
+    """Curved isoparametric wall faces, flux bounce-back, body force (general metrics path)."""
+    mesh = W.pipe_mesh(n_core=2, n_radial=2, n_axial=2, length=1.0)
+    g = (0.0, 0.0, 2e-4)
+    o, s = pair(P, mesh, "D3Q19", 4, 2e-3, filt={"shape": 0, "gamma": 0.1, "kc": 2.0}, g=g)
+    f = random_continuous_state(o, 0.02, 2)
+    f = check_one_step(P, o, s, f, 1e-12)
+    for _ in range(4):
+        f = o.step(f)
+    s.step(4)
+    assert rel(s.get_state(), o.to_local(f)) <= 1e-11
+
+
+def test_box_walls_on_all_faces(P):
+    """Nodes on two and three wall faces (edges and corners of a closed box), moving lid."""
+    mesh = W.box_mesh((2, 3, 2), (0, 0, 0), (1, 1.5, 1), (False, False, False),
+                      walls={0: 1, 1: 1, 2: 1, 3: 2, 4: 1, 5: 1}, wall_velocity=[[0, 0, 0], [0.02, 0, 0.01]])
+    o, s = pair(P, mesh, "D3Q27", 3, 1e-2)
+    f = random_continuous_state(o, 0.01, 3)
+    check_one_step(P, o, s, f, 1e-12)
+
+
+def test_single_periodic_element(P):
+    mesh = W.box_mesh((1, 1), (0, 0), (1, 1), (True, True))
+    o, s = pair(P, mesh, "D2Q9", 6, 1e-2, filt={"shape": 0, "gamma": 0.2, "kc": 3.5})
+    f = random_continuous_state(o, 0.02, 4)
+    f = check_one_step(P, o, s, f, 1e-12)
+    check_one_step(P, o, s, f, 1e-12)
+
+
+@pytest.mark.parametrize("N", [2, 12])
+def test_extreme_orders(P, N):
+    mesh = W.box_mesh((3, 2), (0, 0), (1, 1), (True, False), walls={2: 1, 3: 2},
+                      wall_velocity=[[0, 0], [0.01, 0]])
+    filt = {"shape": 0, "gamma": 0.1, "kc": 1.0} if N == 2 else {"shape": 1, "gamma": 0.1, "kc": 10.0}
+    o, s = pair(P, mesh, "D2Q9", N, 1e-2, filt=filt)
+    f = random_continuous_state(o, 0.02, 5)
+    f = check_one_step(P, o, s, f, 1e-12)
+    check_one_step(P, o, s, f, 1e-12)
+
+
+def test_zero_steps_roundtrip(P):
+    mesh = W.box_mesh((2, 2), (0, 0), (1, 1), (True, True))
+    o, s = pair(P, mesh, "D2Q9", 4, 1e-2, filt={"shape": 0, "gamma": 0.1, "kc": 2.0})
+    f = random_continuous_state(o, 0.02, 6)
+    s.set_state(np.ascontiguousarray(o.to_local(f)))
+    s.step(0)
+    assert rel(s.get_state(), o.to_local(f)) <= 1e-15
+
+
+def test_fp32_deviation_form(P):
+    """FP32 deviations: f within 1e-6 relative after one step; rho, u within FP32 bounds after 100."""
+    mesh = W.box_mesh((4, 4), (0, 0), (1, 1), (True, True))
+    case = W.shear_layer_case(n=4, order=8)
+    o, s = pair(P, mesh, "D2Q9", 8, case.nu, precision=P.FP32DEV, filt=case.filt, init=case.init)
+    f = o.initial_state_from(case.init)
+    f1 = o.step(f)
+    s.step(1)
+    assert rel(s.get_state(), o.to_local(f1)) <= 1e-6
+    f = o.run(f1, 99)
+    s.step(99)
+    rho_o, u_o = o.moments(f)
+    rho_g, u_g = s.moments()
+    assert float(np.abs(rho_g - rho_o[o.glo]).max()) <= 1e-6
+    assert float(np.abs(u_g - u_o[o.glo]).max()) <= 1e-4 * case.U0
