@@ -170,6 +170,20 @@ int selbm_diagnostics(selbm_t *h, double out[8]);
  */
 int selbm_mesh_check(const selbm_mesh *mesh, int32_t lattice, int32_t order, int64_t out_i[6], double out_d[4]);
 
+/*
+ * Per-kernel device timers (tracing).  selbm_timers(h, 1) resets and starts
+ * recording a CUDA event pair around every hot-path launch on the handle's
+ * stream; selbm_timers(h, 0) stops.  selbm_timers_read synchronises the
+ * stream and returns, per kernel kind k, the summed device time ms[k] and the
+ * launch count n[k] since the last reset:
+ *   k = 0: stage kernel, stage 1 (filter + collision + streaming RHS)
+ *   k = 1: stage kernel, stages 2 and 3
+ *   k = 2: assembly kernel (all stages)
+ *   k = 3: reserved
+ */
+int selbm_timers(selbm_t *h, int enable);
+int selbm_timers_read(selbm_t *h, double ms[4], int64_t n[4]);
+
 /* Block until all work on the handle's stream is done; returns the first CUDA error seen. */
 int selbm_sync(selbm_t *h);
 

@@ -25,7 +25,7 @@ ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_MESH", -3: "ERR_CUDA", -4: "ERR_NONFI
 EXPORTS = ["selbm_create", "selbm_destroy", "selbm_last_error", "selbm_info", "selbm_lattice_table",
            "selbm_node_coords", "selbm_init", "selbm_set_state", "selbm_get_state", "selbm_step",
            "selbm_moments", "selbm_set_filter", "selbm_set_body_force", "selbm_diagnostics", "selbm_sync",
-           "selbm_mesh_check"]
+           "selbm_mesh_check", "selbm_timers", "selbm_timers_read"]
 
 
 class SelbmError(RuntimeError):
@@ -80,6 +80,8 @@ def load_library(path: str = LIB_PATH):
     lib.selbm_set_body_force.argtypes = [P, D]
     lib.selbm_diagnostics.argtypes = [P, D]
     lib.selbm_sync.argtypes = [P]
+    lib.selbm_timers.argtypes = [P, I]
+    lib.selbm_timers_read.argtypes = [P, D, C.POINTER(C.c_int64)]
     lib.selbm_mesh_check.argtypes = [C.POINTER(MeshC), C.c_int32, C.c_int32, C.POINTER(C.c_int64), D]
     for name in EXPORTS:
         if name not in ("selbm_destroy", "selbm_last_error"):
@@ -253,6 +255,16 @@ class SELBM:
         out = np.zeros(8)
         self._check(self.lib.selbm_diagnostics(self.h, _dptr(out)))
         return out
+
+    def timers(self, enable=True):
+        self._check(self.lib.selbm_timers(self.h, int(enable)))
+
+    def timers_read(self):
+        """{kind: (ms, launches)} for kinds stage1, stage23, assembly, other."""
+        ms = np.zeros(4)
+        n = np.zeros(4, np.int64)
+        self._check(self.lib.selbm_timers_read(self.h, _dptr(ms), n.ctypes.data_as(C.POINTER(C.c_int64))))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(["stage1", "stage23", "assembly", "other"])}
 
     def sync(self):
         self._check(self.lib.selbm_sync(self.h))

@@ -55,6 +55,28 @@ struct selbm {
   double *d_io = nullptr;  // staging for host <-> device FP64 arrays
   size_t io_bytes = 0;
   std::vector<void *> allocs;
+  // tracing: event pairs around hot-path launches
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+  cudaEvent_t take_event() {
+    if (!ev_pool.empty()) { cudaEvent_t e = ev_pool.back(); ev_pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  cudaEvent_t mark_begin() {
+    if (!timing) return nullptr;
+    cudaEvent_t e = take_event();
+    cudaEventRecord(e, stream);
+    return e;
+  }
+  void mark_end(int kind, cudaEvent_t b) {
+    if (!timing || !b) return;
+    cudaEvent_t e = take_event();
+    cudaEventRecord(e, stream);
+    ev_used.push_back({kind, {b, e}});
+  }
 
   int fail(int code, const std::string &m) { err = m; return code; }
   int cuda_fail(cudaError_t e, const char *where) {
@@ -171,10 +193,14 @@ cudaError_t enqueue_step(selbm *h, bool apply_filter) {
     p.stage = s + 1; p.A = A[s]; p.B = B[s];
     p.apply_filter = (s == 0 && apply_filter) ? 1 : 0;
     p.fin = fin[s]; p.f0 = F0; p.fout = fout[s]; p.f0out = F0;
+    cudaEvent_t t0 = h->mark_begin();
     if ((e = launch_stage<Real>(h->lat, h->S.affine, p, h->stream))) return e;
+    h->mark_end(s == 0 ? 0 : 1, t0);
     KParams<Real> q = p;
     q.fin = (s == 0) ? F0 : fin[s];      // assembly: f^{s-1} on shared nodes (stage 1: f^0)
+    t0 = h->mark_begin();
     if ((e = launch_dss<Real>(h->lat, q, h->stream))) return e;
+    h->mark_end(2, t0);
   }
   return cudaSuccess;
 }
@@ -270,6 +296,8 @@ int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_
 void selbm_destroy(selbm_t *h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  for (auto &u : h->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   for (void *p : h->allocs) cudaFree(p);
   void *own[] = {h->d_l2g, h->d_owner, h->d_bslot, h->d_bnode_g, h->d_bnode_off, h->d_bnode_slot, h->d_first,
                  h->d_mass, h->d_partial, h->d_diag, h->d_io};
@@ -467,6 +495,33 @@ int selbm_mesh_check(const selbm_mesh *mesh, int32_t lattice, int32_t order, int
     for (const WallNode &w : S.walls) ws += w.wsJs;
     out_d[0] = S.min_spacing; out_d[1] = m; out_d[2] = (double)S.walls.size(); out_d[3] = ws;
   }
+  return SELBM_OK;
+}
+
+int selbm_timers(selbm_t *h, int enable) {
+  if (!h) return SELBM_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  for (auto &u : h->ev_used) { h->ev_pool.push_back(u.second.first); h->ev_pool.push_back(u.second.second); }
+  h->ev_used.clear();
+  h->timing = enable != 0;
+  return SELBM_OK;
+}
+
+int selbm_timers_read(selbm_t *h, double ms[4], int64_t n[4]) {
+  if (!h || !ms || !n) return SELBM_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "timers");
+  for (int k = 0; k < 4; ++k) { ms[k] = 0.0; n[k] = 0; }
+  for (auto &u : h->ev_used) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, u.second.first, u.second.second) == cudaSuccess) {
+      ms[u.first] += t;
+      n[u.first] += 1;
+    }
+    h->ev_pool.push_back(u.second.first);
+    h->ev_pool.push_back(u.second.second);
+  }
+  h->ev_used.clear();
   return SELBM_OK;
 }
 
