@@ -184,6 +184,40 @@ int selbm_mesh_check(const selbm_mesh *mesh, int32_t lattice, int32_t order, int
 int selbm_timers(selbm_t *h, int enable);
 int selbm_timers_read(selbm_t *h, double ms[4], int64_t n[4]);
 
+/*
+ * Allocation-free integrals of a caller-owned state.  The paper has no
+ * counterpart: this entry exists for callers that cannot let the library
+ * allocate device memory -- e.g. an application whose own memory pool has
+ * already reserved the GPU's memory, or a per-step monitoring hook inside a
+ * time loop where cudaMalloc/cudaFree would add an implicit device
+ * synchronisation.  selbm_diagnostics needs a handle, and selbm_create
+ * allocates; this call does not allocate anything.
+ *
+ * Inputs (device pointers): f [Q][nelem][np] FP64 populations f_bar at the
+ * element-local nodes (the layout of selbm_get_state), w [nelem][np] the
+ * quadrature weight of each local node (rho_i rho_j rho_k J for conforming
+ * elements, so that copies of a shared node add up to its assembled mass).
+ * Output (device pointer): out[0] = sum w rho, out[1..3] = sum w rho u,
+ * out[4] = sum w rho0 |u|^2 / 2, out[5] = number of non-finite entries of f.
+ * Enqueued on cuda_stream (a cudaStream_t, NULL = legacy default stream);
+ * returns without synchronising.
+ *
+ * Scratch: per-element partial sums in one fixed device array inside the
+ * library (SELBM_NOALLOC_MAX_ELEMS x 6 doubles = 3 MiB), held by every GPU
+ * that loads the library until the process exits.  nelem above
+ * SELBM_NOALLOC_MAX_ELEMS returns SELBM_ERR_ARG with no device work.  Every
+ * call overwrites the partials it reads, so nothing carries over between
+ * calls, but all calls share the one array: calls that overlap on the GPU
+ * (e.g. on two streams at once) race and must be serialised by the caller.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Errors: SELBM_ERR_ARG (NULL pointer, bad sizes
+ * or lattice), SELBM_ERR_CUDA (address lookup or launch failed).
+ */
+#define SELBM_NOALLOC_MAX_ELEMS 65536
+int selbm_integrals_noalloc(int32_t lattice, int32_t nelem, int32_t np, const double *f, const double *w,
+                            double rho0, double *out, void *cuda_stream);
+
 /* Block until all work on the handle's stream is done; returns the first CUDA error seen. */
 int selbm_sync(selbm_t *h);
 
