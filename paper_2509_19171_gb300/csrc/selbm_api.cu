@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -42,13 +43,16 @@ struct selbm {
   double dt = 0, tau = 0, lam = 0, omega = 0, time = 0;
   int64_t steps = 0;
   bool initialized = false, filter_pending = false, filter_on = false, has_force = false;
+  bool use_fast = true;
+  int wall_max = 0;   // SELBM_GENERIC_KERNEL=1 in the environment selects the generic stage kernel
   std::string err;
-  std::vector<double> Fmat, sigma;
+  std::vector<double> Fmat, sigma, FU, FW;
+  int Fr = 0;
   // device buffers (Real = double or float by precision)
   void *FA = nullptr, *F0 = nullptr, *F2 = nullptr, *T = nullptr, *RHO = nullptr, *BUF = nullptr;
   void *d_el_drdx = nullptr, *d_el_J = nullptr, *d_drdx = nullptr, *d_wJ = nullptr, *d_gllw = nullptr;
   void *d_D = nullptr, *d_F = nullptr, *d_wall_u = nullptr, *d_walls = nullptr, *d_minv = nullptr;
-  int32_t *d_l2g = nullptr, *d_bslot = nullptr, *d_bnode_g = nullptr, *d_bnode_off = nullptr, *d_bnode_slot = nullptr;
+  int32_t *d_l2g = nullptr, *d_bslot = nullptr, *d_binv = nullptr, *d_bnode_g = nullptr, *d_bnode_off = nullptr, *d_bnode_slot = nullptr;
   int32_t *d_wall_off = nullptr, *d_first = nullptr;
   uint8_t *d_owner = nullptr;
   double *d_mass = nullptr, *d_partial = nullptr, *d_diag = nullptr;
@@ -152,6 +156,7 @@ cudaError_t upload_real(selbm *h) {
       wp.push_back(w);
     }
     woff[el + 1] = (int32_t)wp.size();
+    h->wall_max = std::max(h->wall_max, woff[el + 1] - woff[el]);
   }
   WallPt<Real> *dw;
   if ((e = upload(&dw, wp))) return e; h->d_walls = dw; if (dw) h->allocs.push_back(dw);
@@ -168,7 +173,8 @@ KParams<Real> base_params(selbm *h) {
   p.dt = (Real)h->dt; p.half_dt = (Real)(0.5 * h->dt); p.omega = (Real)h->omega; p.rho0 = (Real)h->P.rho0;
   for (int k = 0; k < 3; ++k) p.g[k] = (Real)(k < S.dim ? h->P.body_accel[k] : 0.0);
   p.has_force = h->has_force;
-  p.l2g = h->d_l2g; p.owner = h->d_owner; p.bslot = h->d_bslot;
+  p.wall_max = h->wall_max;
+  p.l2g = h->d_l2g; p.owner = h->d_owner; p.bslot = h->d_bslot; p.binv = h->d_binv;
   p.el_drdx = (const Real *)h->d_el_drdx; p.el_J = (const Real *)h->d_el_J;
   p.drdx = (const Real *)h->d_drdx; p.wJ = (const Real *)h->d_wJ; p.gllw = (const Real *)h->d_gllw;
   p.Dm = (const Real *)h->d_D; p.Fm = (const Real *)h->d_F;
@@ -177,6 +183,21 @@ KParams<Real> base_params(selbm *h) {
   p.bnode_minv = (const Real *)h->d_minv;
   p.T = (Real *)h->T; p.rho = (Real *)h->RHO;
   return p;
+}
+
+// register-blocked kernel when compiled for (lattice, N); generic kernel otherwise
+template <typename Real>
+cudaError_t launch_stage_any(selbm *h, const KParams<Real> &p) {
+  if (h->use_fast) {
+    FastHost fh{h->S.gll.D.data(), h->FU.data(), h->FW.data(), h->S.gll.w.data(), h->Fr};
+    cudaError_t err = cudaSuccess;
+    bool done = false;
+    if (h->lat == SELBM_D2Q9) done = launch_fast_d2q9<Real>(h->S.N, h->S.affine, p, fh, h->stream, &err);
+    else if (h->lat == SELBM_D3Q19) done = launch_fast_d3q19<Real>(h->S.N, h->S.affine, p, fh, h->stream, &err);
+    else done = launch_fast_d3q27<Real>(h->S.N, h->S.affine, p, fh, h->stream, &err);
+    if (done) return err;
+  }
+  return launch_stage<Real>(h->lat, h->S.affine, p, h->stream);
 }
 
 // one time step: three stages, each = element kernel + assembly kernel
@@ -194,7 +215,7 @@ cudaError_t enqueue_step(selbm *h, bool apply_filter) {
     p.apply_filter = (s == 0 && apply_filter) ? 1 : 0;
     p.fin = fin[s]; p.f0 = F0; p.fout = fout[s]; p.f0out = F0;
     cudaEvent_t t0 = h->mark_begin();
-    if ((e = launch_stage<Real>(h->lat, h->S.affine, p, h->stream))) return e;
+    if ((e = launch_stage_any<Real>(h, p))) return e;
     h->mark_end(s == 0 ? 0 : 1, t0);
     KParams<Real> q = p;
     q.fin = (s == 0) ? F0 : fin[s];      // assembly: f^{s-1} on shared nodes (stage 1: f^0)
@@ -219,6 +240,7 @@ int set_filter_internal(selbm *h, const selbm_filter &f) {
   if (f.gamma < 0.0 || f.gamma > 1.0) return h->fail(SELBM_ERR_ARG, "filter gamma must be in [0, 1]");
   h->P.filter = f;
   build_filter(h->S.gll, f, &h->Fmat, &h->sigma);
+  build_filter_lowrank(h->S.gll, f, &h->FU, &h->FW, &h->Fr);
   h->filter_on = f.gamma != 0.0;
   cudaError_t e;
   if (h->prec == SELBM_FP64)
@@ -259,6 +281,10 @@ int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_
   h->lat = params->lattice;
   h->prec = params->precision;
   h->rsz = h->prec == SELBM_FP64 ? 8 : 4;
+  {
+    const char *gk = std::getenv("SELBM_GENERIC_KERNEL");
+    h->use_fast = !(gk && gk[0] == '1');
+  }
   std::string err;
   int rc = build_setup(*mesh, params->lattice, params->order, &h->S, &err);
   if (rc != SELBM_OK) { g_create_error = err; delete h; return rc; }
@@ -278,6 +304,12 @@ int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_
   CK(upload(&h->d_l2g, S.l2g));
   CK(upload(&h->d_owner, S.owner));
   CK(upload(&h->d_bslot, S.bslot));
+  {
+    std::vector<int32_t> binv(std::max(S.Nb, 1), 0);
+    for (int i = 0; i < S.Np; ++i)
+      if (S.bslot[i] >= 0) binv[S.bslot[i]] = i;
+    CK(upload(&h->d_binv, binv));
+  }
   CK(upload(&h->d_bnode_g, S.bnode_g));
   CK(upload(&h->d_bnode_off, S.bnode_off));
   CK(upload(&h->d_bnode_slot, S.bnode_slot));
@@ -299,7 +331,7 @@ void selbm_destroy(selbm_t *h) {
   for (auto &u : h->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   for (void *p : h->allocs) cudaFree(p);
-  void *own[] = {h->d_l2g, h->d_owner, h->d_bslot, h->d_bnode_g, h->d_bnode_off, h->d_bnode_slot, h->d_first,
+  void *own[] = {h->d_l2g, h->d_owner, h->d_bslot, h->d_binv, h->d_bnode_g, h->d_bnode_off, h->d_bnode_slot, h->d_first,
                  h->d_mass, h->d_partial, h->d_diag, h->d_io};
   for (void *p : own)
     if (p) cudaFree(p);

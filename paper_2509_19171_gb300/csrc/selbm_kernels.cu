@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(512) stage_kernel(const KParams<Real> p) {
       } else {
         wJi = p.wJ[(size_t)e * Np + i];
       }
-      p.T[a * EN + (size_t)e * p.Nb + b] = -wJi * adv;
+      p.T[a * EN + (size_t)e * p.Nb + b] = -(p.B * p.dt) * wJi * adv;
     }
   }
   // flux bounce-back on the element's wall nodes (Sec. 2.2.1):
@@ -253,36 +253,49 @@ __global__ void __launch_bounds__(512) stage_kernel(const KParams<Real> p) {
           sum += wp.wsJs[f] * ne * jump;
         }
       }
-      p.T[a * EN + (size_t)e * p.Nb + wp.b] += sum;
+      p.T[a * EN + (size_t)e * p.Nb + wp.b] += (p.B * p.dt) * sum;
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// assembly of element-boundary nodes: f^s = A f^0 + B (f^{s-1} + dt (sum_c T_c / M + F*))
-// copies summed in ascending (element, local node) order
+// assembly of element-boundary nodes: f^s = A f^0 + B f^{s-1} + sum_c T_c / M + B dt F*,
+// where T_c = B dt x (weighted contribution of copy c); copies summed in ascending (element, local node) order
 // ---------------------------------------------------------------------------
 template <typename Real, int LAT>
 __global__ void dss_kernel(const KParams<Real> p) {
   constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
-  const size_t total = (size_t)Q * p.Gb;
+  const Real Bdt = p.B * p.dt;
   const size_t EN = (size_t)p.E * p.Nb;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    const int a = (int)(idx / p.Gb), u = (int)(idx - (size_t)a * p.Gb);
-    Real s = 0;
-    const Real *Ta = p.T + a * EN;
-    for (int c = p.bnode_off[u]; c < p.bnode_off[u + 1]; ++c) s += Ta[p.bnode_slot[c]];
+  const Real *__restrict__ Tr = p.T;
+  const Real *__restrict__ fin = p.fin;
+  const Real *__restrict__ f0 = p.f0;
+  Real *__restrict__ fout = p.fout;
+  const size_t G = p.G;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < p.Gb; u += gridDim.x * blockDim.x) {
+    const int c0 = p.bnode_off[u], c1 = p.bnode_off[u + 1];
     const size_t gid = p.bnode_g[u];
-    Real Fs = 0;
-    if (p.has_force) {
-      Real eg = 0;
+    const Real minv = p.bnode_minv[u];
+    const Real rho = p.has_force ? p.rho[gid] : Real(0);
+    Real s[Q];
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) eg += (Real)c_e[LAT][a][k] * p.g[k];
-      Fs = wt<Real>(LAT, a) * eg * p.rho[gid] * Real(3);
+    for (int a = 0; a < Q; ++a) s[a] = 0;
+    for (int c = c0; c < c1; ++c) {
+      const Real *tc = Tr + p.bnode_slot[c];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) s[a] += tc[a * EN];
     }
-    const Real fprev = p.fin[(size_t)a * p.G + gid];
-    const Real f0v = p.f0[(size_t)a * p.G + gid];
-    p.fout[(size_t)a * p.G + gid] = p.A * f0v + p.B * (fprev + p.dt * (s * p.bnode_minv[u] + Fs));
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      Real Fs = 0;
+      if (p.has_force) {
+        Real eg = 0;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) eg += (Real)c_e[LAT][a][k] * p.g[k];
+        Fs = wt<Real>(LAT, a) * eg * rho * Real(3);
+      }
+      fout[(size_t)a * G + gid] = p.A * f0[(size_t)a * G + gid] + p.B * fin[(size_t)a * G + gid] + s[a] * minv + Bdt * Fs;
+    }
   }
 }
 
@@ -341,10 +354,9 @@ cudaError_t launch_stage(int lat, bool affine, const KParams<Real> &p, cudaStrea
 
 template <typename Real, int LAT>
 static cudaError_t launch_dss_t(const KParams<Real> &p, cudaStream_t s) {
-  const size_t total = (size_t)Lat<LAT>::Q * p.Gb;
-  if (total == 0) return cudaSuccess;
+  if (p.Gb == 0) return cudaSuccess;
   const int threads = 256;
-  const int blocks = (int)std::min<size_t>((total + threads - 1) / threads, 152 * 32);
+  const int blocks = (int)std::min<size_t>(((size_t)p.Gb + threads - 1) / threads, 152 * 32);
   dss_kernel<Real, LAT><<<blocks, threads, 0, s>>>(p);
   return cudaGetLastError();
 }

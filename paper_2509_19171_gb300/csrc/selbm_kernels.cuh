@@ -22,9 +22,11 @@ struct KParams {
   Real dt, omega, rho0, half_dt;
   Real g[3];
   int has_force, apply_filter;
+  int wall_max;              // most wall nodes on one element (sizes a shared-memory buffer)
   const int32_t *l2g;        // [E][Np]
   const uint8_t *owner;      // [E][Np]
-  const int32_t *bslot;      // [Np]
+  const int32_t *bslot;      // [Np] boundary slot of each local node, -1 inside
+  const int32_t *binv;       // [Nb] local node of each boundary slot
   const Real *el_drdx;       // [E][dim][dim] affine metrics
   const Real *el_J;          // [E]
   const Real *drdx;          // [E][Np][dim][dim] general metrics
@@ -65,6 +67,18 @@ cudaError_t launch_moments(int lat, const Real *buf, const int32_t *l2g, int G, 
 int diag_blocks();
 template <typename Real>
 cudaError_t launch_diag(int lat, const Real *buf, const double *mass, int G, double rho0, double *partial, double *out, cudaStream_t s);
+
+// host copies of the matrices of the register-blocked stage kernel
+struct FastHost {
+  const double *D, *U, *W, *w;   // D_hat [n][n]; filter F = I + U W (U n x r, W r x n, stride n); GLL weights
+  int r;
+};
+template <typename Real>
+bool launch_fast_d2q9(int N, bool affine, const KParams<Real> &p, const FastHost &f, cudaStream_t s, cudaError_t *err);
+template <typename Real>
+bool launch_fast_d3q19(int N, bool affine, const KParams<Real> &p, const FastHost &f, cudaStream_t s, cudaError_t *err);
+template <typename Real>
+bool launch_fast_d3q27(int N, bool affine, const KParams<Real> &p, const FastHost &f, cudaStream_t s, cudaError_t *err);
 
 void upload_lattice_constants();
 size_t stage_smem_bytes(int lat, int Np, int n, int real_size);

@@ -161,6 +161,30 @@ void build_filter(const GLL &g, const selbm_filter &f, std::vector<double> *F, s
   }
 }
 
+void build_filter_lowrank(const GLL &g, const selbm_filter &f, std::vector<double> *U, std::vector<double> *W, int *r) {
+  const int N = g.N, n = N + 1;
+  std::vector<double> F, sigma;
+  build_filter(g, f, &F, &sigma);
+  std::vector<double> V(n * n), Vi;
+  for (int i = 0; i < n; ++i) {
+    const double x = g.xi[i];
+    std::vector<double> Lk(n);
+    for (int k = 0; k < n; ++k) { double L, dL; legendre_pair(k, x, &L, &dL); Lk[k] = L; }
+    for (int k = 0; k < n; ++k) V[i * n + k] = (k == 0) ? 1.0 : (k == 1 ? x : Lk[k] - Lk[k - 2]);
+  }
+  invert(V, n, &Vi);
+  U->assign(n * n, 0.0);
+  W->assign(n * n, 0.0);
+  int q = 0;
+  for (int k = 0; k < n; ++k) {
+    if (sigma[k] == 1.0) continue;
+    for (int j = 0; j < n; ++j) (*U)[j * n + q] = V[j * n + k];
+    for (int i = 0; i < n; ++i) (*W)[q * n + i] = (sigma[k] - 1.0) * Vi[k * n + i];
+    ++q;
+  }
+  *r = q;
+}
+
 // ---------------------------------------------------------------------------
 // element map (Gordon-Hall blend with circular arcs)
 // ---------------------------------------------------------------------------

@@ -104,13 +104,14 @@ def test_shear_layer_100_steps(P):
     assert abs(d[0] - m) <= 1e-12 * m and abs(d[4] - ke) <= 1e-9 * ke
 
 
-@pytest.mark.parametrize("lat", ["D3Q19", "D3Q27"])
-def test_tgv3d_box_quadratic_filter(P, lat):
+@pytest.mark.parametrize("lat,N", [("D3Q19", 5), ("D3Q27", 5), ("D3Q27", 7), ("D3Q19", 7)])
+def test_tgv3d_box_quadratic_filter(P, lat, N):
     L = 2 * math.pi
-    mesh = W.box_mesh((3, 2, 2), (0, 0, 0), (L, L, L), (True, True, True))
-    filt = {"shape": 0, "gamma": 0.1, "kc": 3.0}
+    shape = (3, 2, 2) if N == 5 else (2, 2, 2)
+    mesh = W.box_mesh(shape, (0, 0, 0), (L, L, L), (True, True, True))
+    filt = {"shape": 0, "gamma": 0.1, "kc": float(N - 2)}
     init = W.tgv3d_init(0.05)
-    o, s = pair(P, mesh, lat, 5, 0.05 / 1600, filt=filt, init=init)
+    o, s = pair(P, mesh, lat, N, 0.05 / 1600, filt=filt, init=init)
     f = o.initial_state_from(init)
     f = o.step(f)
     s.step(1)
@@ -120,11 +121,17 @@ def test_tgv3d_box_quadratic_filter(P, lat):
     assert rel(s.get_state(), o.to_local(f)) <= 1e-11
 
 
-def test_pipe_curved_walls_force(P):
-    """Curved isoparametric wall faces, flux bounce-back, body force (general metrics path)."""
-    mesh = W.pipe_mesh(n_core=2, n_radial=2, n_axial=2, length=1.0)
+@pytest.mark.parametrize("N,prec", [(4, 0), (7, 0), (7, 1)])
+def test_pipe_curved_walls_force(P, N, prec):
+    """Curved isoparametric wall faces, flux bounce-back, body force (general metrics path);
+    FP32 deviations (prec 1) within 1e-6 relative after one step."""
+    mesh = W.pipe_mesh(n_core=2, n_radial=2, n_axial=2 if N == 4 else 1, length=1.0)
     g = (0.0, 0.0, 2e-4)
-    o, s = pair(P, mesh, "D3Q19", 4, 2e-3, filt={"shape": 0, "gamma": 0.1, "kc": 2.0}, g=g)
+    o, s = pair(P, mesh, "D3Q19", N, 2e-3, precision=prec, filt={"shape": 0, "gamma": 0.1, "kc": float(N - 2)}, g=g)
+    if prec == 1:
+        f = random_continuous_state(o, 0.02, 2)
+        check_one_step(P, o, s, f, 1e-6)
+        return
     f = random_continuous_state(o, 0.02, 2)
     f = check_one_step(P, o, s, f, 1e-12)
     for _ in range(4):
@@ -168,6 +175,17 @@ def test_zero_steps_roundtrip(P):
     s.set_state(np.ascontiguousarray(o.to_local(f)))
     s.step(0)
     assert rel(s.get_state(), o.to_local(f)) <= 1e-15
+
+
+def test_generic_kernel_matches_oracle(P, monkeypatch):
+    """The generic (runtime-order) stage kernel at an order that also has a register-blocked kernel."""
+    monkeypatch.setenv("SELBM_GENERIC_KERNEL", "1")
+    L = 2 * math.pi
+    mesh = W.box_mesh((2, 2, 2), (0, 0, 0), (L, L, L), (True, True, True))
+    o, s = pair(P, mesh, "D3Q27", 7, 1e-3, filt={"shape": 0, "gamma": 0.1, "kc": 5.0})
+    f = random_continuous_state(o, 0.03, 8)
+    f = check_one_step(P, o, s, f, 1e-12)
+    check_one_step(P, o, s, f, 1e-12)
 
 
 def test_fp32_deviation_form(P):
