@@ -19,8 +19,8 @@ Readings of the paper taken here (each one listed in the design doc):
 * The geometric factor G_lk = rho rho rho J dr_l/dx_k (chain rule).
 * No flux at interior element faces; assembly only (continuous Galerkin).
 * The filter is applied once per step after the last stage, element by
-  element; at shared nodes the copies agree in exact arithmetic and the
-  oracle stores their mean.
+  element; the copies of a shared node are reconciled by their
+  mass-weighted average (they agree when every element has the same filter).
 * F = rho g with rho from the step's moments, frozen through the stages.
 """
 import numpy as np
@@ -149,17 +149,59 @@ class OracleSELBM:
         return f0 / 3.0 + 2.0 / 3.0 * (f2 + dt * self.rhs(f2, Fstar))
 
     # ----------------------------------------------------------------- filter
+    def assemble_average(self, fl):
+        """Element copies [Q, E, Np] -> unique nodes: mass-weighted average sum_c wJ_c f_c / M.
+        With the same filter in every element the copies agree and this returns their value;
+        with element-dependent filters it keeps the total mass, since each element's filter
+        keeps its own integral."""
+        out = np.zeros((self.Q, self.G))
+        for a in range(self.Q):
+            np.add.at(out[a], self.glo.ravel(), (self.wJ * fl[a]).ravel())
+        return out / self.mass[None, :]
+
     def apply_filter(self, f):
-        """(F x F (x F)) f_alpha element by element (Sec. 2.4); shared nodes take the mean of their copies."""
+        """(F x F (x F)) f_alpha element by element (Sec. 2.4), then the copies of shared
+        nodes are reconciled by their mass-weighted average."""
         if not self.filter_on:
             return f
         fl = self.to_local(f)
         for l in range(self.dim):
             fl = geo.apply_axis(self.Fmat, fl, l, self.N, self.dim)
-        out = np.zeros_like(f)
-        for a in range(self.Q):
-            np.add.at(out[a], self.glo.ravel(), fl[a].ravel())
-        return out / self.copies[None, :]
+        return self.assemble_average(fl)
+
+    def apply_filter_elements(self, f, sigma_e):
+        """Filter with a per-element transfer function sigma_e [E, N+1] (learned control);
+        shared nodes take the mass-weighted average of their copies."""
+        V = gll.modal_basis(self.N, self.xi)
+        Vi = np.linalg.inv(V)
+        fl = self.to_local(f).copy()
+        rows, inv = np.unique(np.round(sigma_e, 15), axis=0, return_inverse=True)
+        for r in range(len(rows)):
+            es = np.nonzero(inv.ravel() == r)[0]
+            F = V @ np.diag(sigma_e[es[0]]) @ Vi
+            sub = fl[:, es]
+            for l in range(self.dim):
+                sub = geo.apply_axis(F, sub, l, self.N, self.dim)
+            fl[:, es] = sub
+        return self.assemble_average(fl)
+
+    def learned_sigma(self, f, params, lo, hi):
+        """Per-element transfer functions from the learned control (features of f, BF16
+        weights, FP64 arithmetic); elements whose features leave [lo, hi] keep the fixed filter."""
+        from . import learned as L
+        rho, u = self.moments(f)
+        x = L.features(rho[self.glo], u[self.glo], self.rho0, self.N, self.dim)
+        gam, kc, inr = L.infer_filter(params, x, lo, hi, self.N)
+        sig = np.array([gll.filter_sigma(self.N, 0, g, k) if ok else self.sigma
+                        for g, k, ok in zip(gam, kc, inr)])
+        return sig, x, inr
+
+    def step_learned(self, f, params, lo, hi):
+        """One step whose end-of-step filter is chosen per element by the learned control."""
+        f0, Fstar = self.collide(f)
+        f3 = self.ssprk3(f0, Fstar)
+        sig, _, _ = self.learned_sigma(f3, params, lo, hi)
+        return self.apply_filter_elements(f3, sig)
 
     # ------------------------------------------------------------------- step
     def step(self, f):
