@@ -160,6 +160,61 @@ int selbm_set_body_force(selbm_t *h, const double g[3]);
  */
 int selbm_diagnostics(selbm_t *h, double out[8]);
 
+/* ------------------------------------------------------------------------
+ * Learned per-element filter control.  Not in the paper, whose fixed explicit
+ * filter (Sec. 2.4) is the fallback.  Per element and step, before the filter:
+ * features x = [log10(E_k(rho - rho0) + 1e-30), log10(E_k(|u|) + 1e-30)], k = 0..N,
+ * with E_k the sum of squared modal coefficients (hierarchical basis of the
+ * filter) whose largest index is k; scaled input s = 2 (x - lo)/(hi - lo) - 1;
+ * network 2(N+1) -> 64 tanh -> 64 tanh -> 2 with bfloat16 weights (FP32
+ * arithmetic in the FP32 form, FP64 in the FP64 form); gamma = 0.5
+ * sigmoid(o0), kc = 2 + (N-3) sigmoid(o1); the element is filtered with the
+ * paper's quadratic transfer function at (gamma, kc).  Parameter vector (FP32):
+ * W1[64][nin], b1[64], W2[64][64], b2[64], W3[2][64], b3[2], nin = 2(N+1).
+ * Fallback to the fixed filter: per element when any feature leaves [lo, hi];
+ * for the rest of the run when the relative change of the mass between steps
+ * exceeds mass_bound, or (runs without body force, ke_bound > 0) the kinetic
+ * energy grows by more than ke_bound relative between steps; ke_bound <= 0
+ * disables the kinetic-energy criterion (weakly compressible runs exchange
+ * kinetic and acoustic energy, so it is off by default in the binding).
+ * ------------------------------------------------------------------------ */
+
+/* Enable the learned control (host arrays: params [selbm_mlp_nparams(2(N+1))],
+ * lo/hi [2(N+1)]).  Weights are rounded to bfloat16 (nearest, ties to even). */
+int selbm_set_learned_filter(selbm_t *h, const float *params, const float *lo, const float *hi, double mass_bound,
+                             double ke_bound);
+/* Back to the fixed filter. */
+int selbm_clear_learned_filter(selbm_t *h);
+/* out[0] = global fallback flag, out[1] = element-steps that kept the fixed filter
+ * since the last call (counter reset), out[2] = 1 if the learned control is on. */
+int selbm_learned_status(selbm_t *h, int64_t out[4]);
+/* Transfer functions sigma[E][N+1] chosen by the last control pass (host buffer). */
+int selbm_element_sigma(selbm_t *h, double *sigma);
+/* Features of the state the next filter acts on (the state before the pending filter of
+ * the last step, i.e. what the learned control sees), device buffer feat[E][2(N+1)] (float). */
+int selbm_features(selbm_t *h, float *feat);
+/* Per-element error sum wJ ((rho - rho_ref)^2 + |u - u_ref|^2) of h against ref, a
+ * handle on the same mesh at a higher order whose fields are interpolated element by
+ * element to h's GLL nodes; device buffer err[E] (double).  Allocates temporaries. */
+int selbm_element_errors(selbm_t *h, selbm_t *ref, double *err);
+
+/* MLP training (device pointers; scaled inputs x [M][nin], targets y [M][2] = (gamma*, kc*)).
+ * loss = mean(((gamma - gamma*)/0.5)^2 + ((kc - kc*)/(N-3))^2). */
+int selbm_mlp_nparams(int32_t nin);
+/* Mean loss and its gradient over all M samples (FP32, deterministic order). */
+int selbm_mlp_grad(const float *params, int32_t nin, int32_t order, const float *x, const float *y, int64_t M,
+                   float *grad, float *loss, void *cuda_stream);
+/* (gamma, kc) per sample -> out [M][2]; bf16 = 1 rounds the weights to bfloat16. */
+int selbm_mlp_forward(const float *params, int32_t nin, int32_t order, const float *x, int64_t M, int32_t bf16,
+                      float *out, void *cuda_stream);
+/* Adam (0.9, 0.999, 1e-8) on minibatches of `batch` samples in a fresh shuffled order per
+ * epoch (Feistel permutation keyed by seed and epoch); *adam_t counts updates (in/out);
+ * loss_hist (host, [epochs], may be NULL) gets the mean minibatch loss per epoch.
+ * Allocates its scratch. */
+int selbm_mlp_train(float *params, float *m, float *v, int32_t nin, int32_t order, const float *x, const float *y,
+                    int64_t M, int32_t batch, int32_t epochs, float lr, uint64_t seed, int64_t *adam_t,
+                    float *loss_hist, void *cuda_stream);
+
 /*
  * Dry run of selbm_create's host setup, without touching the GPU: validates
  * the mesh and reports out_i[0..5] = E, Np, Q, G (unique nodes), Gb (nodes on
@@ -179,7 +234,7 @@ int selbm_mesh_check(const selbm_mesh *mesh, int32_t lattice, int32_t order, int
  *   k = 0: stage kernel, stage 1 (filter + collision + streaming RHS)
  *   k = 1: stage kernel, stages 2 and 3
  *   k = 2: assembly kernel (all stages)
- *   k = 3: reserved
+ *   k = 3: learned filter control (features, network, drift check)
  */
 int selbm_timers(selbm_t *h, int enable);
 int selbm_timers_read(selbm_t *h, double ms[4], int64_t n[4]);

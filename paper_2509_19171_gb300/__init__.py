@@ -25,7 +25,9 @@ ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_MESH", -3: "ERR_CUDA", -4: "ERR_NONFI
 EXPORTS = ["selbm_create", "selbm_destroy", "selbm_last_error", "selbm_info", "selbm_lattice_table",
            "selbm_node_coords", "selbm_init", "selbm_set_state", "selbm_get_state", "selbm_step",
            "selbm_moments", "selbm_set_filter", "selbm_set_body_force", "selbm_diagnostics", "selbm_sync",
-           "selbm_mesh_check", "selbm_timers", "selbm_timers_read"]
+           "selbm_mesh_check", "selbm_timers", "selbm_timers_read", "selbm_set_learned_filter",
+           "selbm_clear_learned_filter", "selbm_learned_status", "selbm_element_sigma", "selbm_features",
+           "selbm_element_errors", "selbm_mlp_nparams", "selbm_mlp_grad", "selbm_mlp_forward", "selbm_mlp_train"]
 
 
 class SelbmError(RuntimeError):
@@ -80,6 +82,18 @@ def load_library(path: str = LIB_PATH):
     lib.selbm_set_body_force.argtypes = [P, D]
     lib.selbm_diagnostics.argtypes = [P, D]
     lib.selbm_sync.argtypes = [P]
+    F = C.POINTER(C.c_float)
+    lib.selbm_set_learned_filter.argtypes = [P, F, F, F, C.c_double, C.c_double]
+    lib.selbm_clear_learned_filter.argtypes = [P]
+    lib.selbm_learned_status.argtypes = [P, C.POINTER(C.c_int64)]
+    lib.selbm_element_sigma.argtypes = [P, D]
+    lib.selbm_features.argtypes = [P, P]
+    lib.selbm_element_errors.argtypes = [P, P, P]
+    lib.selbm_mlp_nparams.argtypes = [C.c_int32]
+    lib.selbm_mlp_grad.argtypes = [P, C.c_int32, C.c_int32, P, P, C.c_int64, P, P, P]
+    lib.selbm_mlp_forward.argtypes = [P, C.c_int32, C.c_int32, P, C.c_int64, C.c_int32, P, P]
+    lib.selbm_mlp_train.argtypes = [P, P, P, C.c_int32, C.c_int32, P, P, C.c_int64, C.c_int32, C.c_int32,
+                                    C.c_float, C.c_uint64, C.POINTER(C.c_int64), F, P]
     lib.selbm_timers.argtypes = [P, I]
     lib.selbm_timers_read.argtypes = [P, D, C.POINTER(C.c_int64)]
     lib.selbm_mesh_check.argtypes = [C.POINTER(MeshC), C.c_int32, C.c_int32, C.POINTER(C.c_int64), D]
@@ -268,6 +282,92 @@ class SELBM:
 
     def sync(self):
         self._check(self.lib.selbm_sync(self.h))
+
+    # ------------------------------------------------------- learned control
+    def set_learned_filter(self, params, lo, hi, mass_bound=1e-6, ke_bound=0.0):
+        p = np.ascontiguousarray(params, np.float32)
+        l = np.ascontiguousarray(lo, np.float32)
+        u = np.ascontiguousarray(hi, np.float32)
+        F = C.POINTER(C.c_float)
+        self._check(self.lib.selbm_set_learned_filter(self.h, p.ctypes.data_as(F), l.ctypes.data_as(F),
+                                                      u.ctypes.data_as(F), float(mass_bound), float(ke_bound)))
+
+    def clear_learned_filter(self):
+        self._check(self.lib.selbm_clear_learned_filter(self.h))
+
+    def learned_status(self):
+        out = np.zeros(4, np.int64)
+        self._check(self.lib.selbm_learned_status(self.h, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return {"fallback_flag": int(out[0]), "fixed_element_steps": int(out[1]), "enabled": bool(out[2])}
+
+    def element_sigma(self):
+        out = np.zeros((self.E, self.N + 1))
+        self._check(self.lib.selbm_element_sigma(self.h, _dptr(out)))
+        return out
+
+    def features(self, out=None):
+        """Element features [E, 2(N+1)] (float32 CUDA tensor)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.E, 2 * (self.N + 1)), dtype=torch.float32, device="cuda")
+        self._check(self.lib.selbm_features(self.h, C.c_void_p(out.data_ptr())))
+        return out
+
+    def element_errors(self, ref, out=None):
+        """Per-element error against a higher-order handle on the same mesh (float64 CUDA tensor [E])."""
+        import torch
+        if out is None:
+            out = torch.empty(self.E, dtype=torch.float64, device="cuda")
+        self._check(self.lib.selbm_element_errors(self.h, ref.h, C.c_void_p(out.data_ptr())))
+        return out
+
+
+# --------------------------------------------------------------------------- MLP
+def _cur_stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _chk(rc, what):
+    if rc != 0:
+        raise SelbmError(rc, what)
+
+
+def mlp_nparams(nin):
+    return int(load_library().selbm_mlp_nparams(int(nin)))
+
+
+def mlp_grad(params, x, y, order):
+    """(loss, grad) over all samples; params, x, y float32 CUDA tensors."""
+    import torch
+    lib = load_library()
+    grad = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    _chk(lib.selbm_mlp_grad(C.c_void_p(params.data_ptr()), x.shape[1], int(order), C.c_void_p(x.data_ptr()),
+                            C.c_void_p(y.data_ptr()), x.shape[0], C.c_void_p(grad.data_ptr()),
+                            C.c_void_p(loss.data_ptr()), _cur_stream()), "mlp_grad")
+    return float(loss.item()), grad
+
+
+def mlp_forward(params, x, order, bf16=True):
+    import torch
+    lib = load_library()
+    out = torch.empty((x.shape[0], 2), dtype=torch.float32, device=x.device)
+    _chk(lib.selbm_mlp_forward(C.c_void_p(params.data_ptr()), x.shape[1], int(order), C.c_void_p(x.data_ptr()),
+                               x.shape[0], int(bf16), C.c_void_p(out.data_ptr()), _cur_stream()), "mlp_forward")
+    return out
+
+
+def mlp_train(params, m, v, x, y, order, batch=1024, epochs=10, lr=1e-3, seed=0, adam_t=0):
+    """Adam training in place on CUDA tensors; returns (per-epoch mean loss, adam_t)."""
+    lib = load_library()
+    hist = np.zeros(max(epochs, 1), np.float32)
+    t = C.c_int64(int(adam_t))
+    _chk(lib.selbm_mlp_train(C.c_void_p(params.data_ptr()), C.c_void_p(m.data_ptr()), C.c_void_p(v.data_ptr()),
+                             x.shape[1], int(order), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.shape[0],
+                             int(batch), int(epochs), float(lr), int(seed), C.byref(t),
+                             hist.ctypes.data_as(C.POINTER(C.c_float)), _cur_stream()), "mlp_train")
+    return hist[:epochs].tolist(), int(t.value)
 
 
 def from_case(case, precision=FP64, **kw):

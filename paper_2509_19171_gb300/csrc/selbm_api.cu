@@ -12,6 +12,7 @@
 
 #include "../../include/selbm.h"
 #include "selbm_kernels.cuh"
+#include "selbm_learn.cuh"
 #include "selbm_setup.h"
 
 using namespace slb;
@@ -44,6 +45,14 @@ struct selbm {
   int64_t steps = 0;
   bool initialized = false, filter_pending = false, filter_on = false, has_force = false;
   bool use_fast = true;
+  // learned per-element filter control
+  bool learned = false;
+  int nin = 0;
+  double mass_bound = 1e-6, ke_bound = 1e-6;
+  void *d_Vm = nullptr, *d_Vinv = nullptr, *d_sigma_e = nullptr, *d_lo = nullptr, *d_hi = nullptr, *d_fixsig = nullptr;
+  __nv_bfloat16 *d_W = nullptr;
+  double *d_acc = nullptr;
+  int *d_flag = nullptr, *d_nfb = nullptr;
   int wall_max = 0;   // SELBM_GENERIC_KERNEL=1 in the environment selects the generic stage kernel
   std::string err;
   std::vector<double> Fmat, sigma, FU, FW;
@@ -128,6 +137,20 @@ cudaError_t upload_real(selbm *h) {
   if ((e = upload(&p, cast_vec<Real>(S.gll.w)))) return e; h->d_gllw = p; h->allocs.push_back(p);
   if ((e = upload(&p, cast_vec<Real>(S.gll.D)))) return e; h->d_D = p; h->allocs.push_back(p);
   if ((e = alloc(&h->d_F, S.n1 * S.n1 * sizeof(Real)))) return e;
+  {
+    std::vector<double> V, Vi;
+    build_modal(S.gll, &V, &Vi);
+    if ((e = upload(&p, cast_vec<Real>(V)))) return e; h->d_Vm = p; h->allocs.push_back(p);
+    if ((e = upload(&p, cast_vec<Real>(Vi)))) return e; h->d_Vinv = p; h->allocs.push_back(p);
+  }
+  if ((e = alloc(&h->d_sigma_e, (size_t)S.E * S.n1 * sizeof(Real)))) return e;
+  if ((e = alloc(&h->d_fixsig, S.n1 * sizeof(Real)))) return e;
+  if ((e = alloc(&h->d_lo, 2 * S.n1 * sizeof(Real)))) return e;
+  if ((e = alloc(&h->d_hi, 2 * S.n1 * sizeof(Real)))) return e;
+  if ((e = alloc((void **)&h->d_acc, 8 * sizeof(double)))) return e;
+  if ((e = alloc((void **)&h->d_flag, 2 * sizeof(int)))) return e;
+  if ((e = alloc((void **)&h->d_nfb, 2 * sizeof(int)))) return e;
+  if ((e = alloc((void **)&h->d_W, (size_t)mlp_nparams(2 * S.n1) * sizeof(__nv_bfloat16)))) return e;
   std::vector<double> wu = S.wall_u;
   if (wu.empty()) wu.assign(3, 0.0);
   if ((e = upload(&p, cast_vec<Real>(wu)))) return e; h->d_wall_u = p; h->allocs.push_back(p);
@@ -185,6 +208,34 @@ KParams<Real> base_params(selbm *h) {
   return p;
 }
 
+// learned filter pass: per-element transfer functions from the features of `f`
+// (the state the pending filter acts on), filtered interior nodes into `out`,
+// weighted shares of boundary nodes into the trace, then their mass-weighted
+// assembly into `out` (the drift check runs after the pass when requested)
+template <typename Real>
+cudaError_t enqueue_learned_filter(selbm *h, const Real *f, Real *out, bool with_drift) {
+  const Setup &S = h->S;
+  ControlArgs<Real> c{};
+  c.E = S.E; c.Np = S.Np; c.n = S.n1; c.N = S.N; c.G = S.G; c.Nb = S.Nb;
+  c.l2g = h->d_l2g; c.bslot = h->d_bslot; c.f = f; c.rho0 = h->P.rho0; c.affine = S.affine ? 1 : 0;
+  c.el_J = (const Real *)h->d_el_J; c.wJ = (const Real *)h->d_wJ; c.gllw = (const Real *)h->d_gllw;
+  c.Vm = (const Real *)h->d_Vm; c.Vinv = (const Real *)h->d_Vinv; c.W = h->d_W;
+  c.lo = (const Real *)h->d_lo; c.hi = (const Real *)h->d_hi; c.fixed_sigma = (const Real *)h->d_fixsig;
+  c.flag = h->d_flag; c.acc = with_drift ? h->d_acc : nullptr;
+  c.sigma_out = (Real *)h->d_sigma_e; c.feat_out = nullptr; c.n_fallback = with_drift ? h->d_nfb : nullptr;
+  c.fout = out; c.T = (Real *)h->T;
+  cudaError_t e = launch_control<Real>(h->lat, c, h->stream);
+  if (e == cudaSuccess && with_drift)
+    e = launch_drift_check(h->d_acc, h->d_flag, h->mass_bound, h->ke_bound, h->has_force ? 0 : 1, h->stream);
+  if (e == cudaSuccess) {
+    KParams<Real> q = base_params<Real>(h);
+    q.A = Real(0); q.B = Real(0); q.has_force = 0; q.dt = Real(0);
+    q.fin = out; q.f0 = out; q.fout = out;
+    e = launch_dss<Real>(h->lat, q, h->stream);
+  }
+  return e;
+}
+
 // register-blocked kernel when compiled for (lattice, N); generic kernel otherwise
 template <typename Real>
 cudaError_t launch_stage_any(selbm *h, const KParams<Real> &p) {
@@ -210,6 +261,13 @@ cudaError_t enqueue_step(selbm *h, bool apply_filter) {
   const Real *fin[3] = {FA, FA, F2};   // element-kernel input f^{s-1} (stage 1: f^3 of the last step)
   Real *fout[3] = {FA, F2, FA};
   cudaError_t e;
+  if (apply_filter && h->learned) {
+    // the learned control filters the pending state in its own pass; stage 1 then skips the filter
+    cudaEvent_t t0 = h->mark_begin();
+    if ((e = enqueue_learned_filter<Real>(h, FA, FA, true))) return e;
+    h->mark_end(3, t0);
+    apply_filter = false;
+  }
   for (int s = 0; s < 3; ++s) {
     p.stage = s + 1; p.A = A[s]; p.B = B[s];
     p.apply_filter = (s == 0 && apply_filter) ? 1 : 0;
@@ -231,6 +289,7 @@ cudaError_t enqueue_finalize(selbm *h) {
   KParams<Real> p = base_params<Real>(h);
   p.fin = (const Real *)h->FA;
   p.fout = (Real *)h->BUF;
+  if (h->filter_pending && h->learned) return enqueue_learned_filter<Real>(h, (const Real *)h->FA, (Real *)h->BUF, false);
   p.apply_filter = (h->filter_pending && h->filter_on) ? 1 : 0;
   return launch_finalize<Real>(h->lat, p, h->stream);
 }
@@ -251,6 +310,13 @@ int set_filter_internal(selbm *h, const selbm_filter &f) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) {
+    if (h->prec == SELBM_FP64) e = cudaMemcpy(h->d_fixsig, h->sigma.data(), h->sigma.size() * 8, cudaMemcpyHostToDevice);
+    else {
+      std::vector<float> sg(h->sigma.begin(), h->sigma.end());
+      e = cudaMemcpy(h->d_fixsig, sg.data(), sg.size() * 4, cudaMemcpyHostToDevice);
+    }
+  }
   if (e != cudaSuccess) return h->cuda_fail(e, "set_filter");
   return SELBM_OK;
 }
@@ -439,7 +505,7 @@ int selbm_step(selbm_t *h, int64_t nsteps) {
   if (!h->initialized) return h->fail(SELBM_ERR_STATE, "state not initialised");
   if (nsteps < 0) return h->fail(SELBM_ERR_ARG, "nsteps < 0");
   for (int64_t k = 0; k < nsteps; ++k) {
-    const bool filt = h->filter_pending && h->filter_on;
+    const bool filt = h->filter_pending && (h->filter_on || h->learned);
     cudaError_t e = h->prec == SELBM_FP64 ? enqueue_step<double>(h, filt) : enqueue_step<float>(h, filt);
     if (e != cudaSuccess) return h->cuda_fail(e, "step");
     h->filter_pending = true;
@@ -474,7 +540,7 @@ int selbm_moments(selbm_t *h, double *rho, double *u, int on_device) {
 
 int selbm_set_filter(selbm_t *h, const selbm_filter *f) {
   if (!h || !f) return SELBM_ERR_ARG;
-  if (h->filter_pending && h->filter_on) {
+  if (h->filter_pending && (h->filter_on || h->learned)) {
     // the last step's filter (old settings) must be applied before switching
     int rc = finalize(h);
     if (rc) return rc;
@@ -555,6 +621,176 @@ int selbm_timers_read(selbm_t *h, double ms[4], int64_t n[4]) {
   }
   h->ev_used.clear();
   return SELBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// learned per-element filter control
+// ---------------------------------------------------------------------------
+static uint16_t float_to_bf16_bits(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  if ((b & 0x7F800000u) == 0x7F800000u) return (uint16_t)(b >> 16);   // inf / nan unchanged
+  b += 0x7FFFu + ((b >> 16) & 1u);                                    // round to nearest, ties to even
+  return (uint16_t)(b >> 16);
+}
+
+int selbm_set_learned_filter(selbm_t *h, const float *params, const float *lo, const float *hi, double mass_bound,
+                             double ke_bound) {
+  if (!h || !params || !lo || !hi) return SELBM_ERR_ARG;
+  const int nin = 2 * h->S.n1, P = mlp_nparams(nin);
+  if (control_smem_bytes(h->lat, h->S.Np, h->S.n1, h->rsz) > 227 * 1024)
+    return h->fail(SELBM_ERR_ARG, "learned filter: element tile does not fit in shared memory (use FP32 or a lower order)");
+  for (int i = 0; i < nin; ++i)
+    if (!(hi[i] > lo[i])) return h->fail(SELBM_ERR_ARG, "learned filter: hi must exceed lo for every feature");
+  if (h->filter_pending && (h->filter_on || h->learned)) {
+    // apply the pending filter with the old settings first
+    int rc = finalize(h);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(h->FA, h->BUF, (size_t)h->Q * h->S.G * h->rsz, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "set_learned_filter");
+    h->filter_pending = false;
+  }
+  std::vector<uint16_t> wb(P);
+  for (int i = 0; i < P; ++i) wb[i] = float_to_bf16_bits(params[i]);
+  cudaError_t e = cudaMemcpyAsync(h->d_W, wb.data(), P * 2, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) {
+    if (h->prec == SELBM_FP64) {
+      std::vector<double> l(lo, lo + nin), u(hi, hi + nin);
+      e = cudaMemcpyAsync(h->d_lo, l.data(), nin * 8, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_hi, u.data(), nin * 8, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    } else {
+      e = cudaMemcpyAsync(h->d_lo, lo, nin * 4, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_hi, hi, nin * 4, cudaMemcpyHostToDevice, h->stream);
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc, 0, 8 * sizeof(double), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flag, 0, 2 * sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_nfb, 0, 2 * sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "set_learned_filter");
+  h->nin = nin;
+  h->mass_bound = mass_bound;
+  h->ke_bound = ke_bound;
+  h->learned = true;
+  return SELBM_OK;
+}
+
+int selbm_clear_learned_filter(selbm_t *h) {
+  if (!h) return SELBM_ERR_ARG;
+  if (h->learned && h->filter_pending) {
+    int rc = finalize(h);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(h->FA, h->BUF, (size_t)h->Q * h->S.G * h->rsz, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "clear_learned_filter");
+    h->filter_pending = false;
+  }
+  h->learned = false;
+  return SELBM_OK;
+}
+
+int selbm_learned_status(selbm_t *h, int64_t out[4]) {
+  if (!h || !out) return SELBM_ERR_ARG;
+  int flag[2] = {0, 0}, nfb[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(flag, h->d_flag, sizeof(flag), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(nfb, h->d_nfb, sizeof(nfb), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_nfb, 0, sizeof(nfb), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "learned_status");
+  out[0] = flag[0]; out[1] = nfb[0]; out[2] = h->learned ? 1 : 0; out[3] = 0;
+  return SELBM_OK;
+}
+
+int selbm_element_sigma(selbm_t *h, double *sigma) {
+  if (!h || !sigma) return SELBM_ERR_ARG;
+  const size_t cnt = (size_t)h->S.E * h->S.n1;
+  cudaError_t e;
+  if (h->prec == SELBM_FP64) {
+    e = cudaMemcpyAsync(sigma, h->d_sigma_e, cnt * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  } else {
+    std::vector<float> tmp(cnt);
+    e = cudaMemcpyAsync(tmp.data(), h->d_sigma_e, cnt * 4, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    for (size_t i = 0; i < cnt; ++i) sigma[i] = tmp[i];
+  }
+  if (e != cudaSuccess) return h->cuda_fail(e, "element_sigma");
+  return SELBM_OK;
+}
+
+int selbm_features(selbm_t *h, float *feat) {
+  if (!h || !feat) return SELBM_ERR_ARG;
+  if (!h->initialized) return h->fail(SELBM_ERR_STATE, "state not initialised");
+  cudaError_t e;
+  auto run = [&](auto tag) {
+    using Real = decltype(tag);
+    const Setup &S = h->S;
+    ControlArgs<Real> c{};
+    c.E = S.E; c.Np = S.Np; c.n = S.n1; c.N = S.N; c.G = S.G; c.Nb = S.Nb;
+    c.l2g = h->d_l2g; c.bslot = h->d_bslot; c.f = (const Real *)h->FA; c.rho0 = h->P.rho0; c.affine = S.affine ? 1 : 0;
+    c.el_J = (const Real *)h->d_el_J; c.wJ = (const Real *)h->d_wJ; c.gllw = (const Real *)h->d_gllw;
+    c.Vm = (const Real *)h->d_Vm; c.Vinv = (const Real *)h->d_Vinv; c.W = nullptr; c.sigma_out = nullptr; c.feat_out = feat;
+    return launch_control<Real>(h->lat, c, h->stream);
+  };
+  e = h->prec == SELBM_FP64 ? run(double()) : run(float());
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "features");
+  return SELBM_OK;
+}
+
+int selbm_element_errors(selbm_t *h, selbm_t *ref, double *err) {
+  if (!h || !ref || !err) return SELBM_ERR_ARG;
+  if (h->S.E != ref->S.E || h->S.dim != ref->S.dim) return h->fail(SELBM_ERR_ARG, "element_errors: meshes differ");
+  const int dim = h->S.dim;
+  const size_t nl = h->nloc(), nlr = ref->nloc();
+  double *buf = nullptr, *I = nullptr, *wq = nullptr;
+  cudaError_t e = cudaMalloc((void **)&buf, (nl + nlr) * (1 + dim) * sizeof(double));
+  std::vector<double> Ih;
+  build_interp(ref->S.N, h->S.N, &Ih);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&I, Ih.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&wq, nl * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(I, Ih.data(), Ih.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(wq, h->S.wJ.data(), nl * sizeof(double), cudaMemcpyHostToDevice);
+  int rc = SELBM_OK;
+  if (e == cudaSuccess) {
+    double *rho = buf, *u = buf + nl, *rhoR = buf + nl * (1 + dim), *uR = rhoR + nlr;
+    rc = selbm_moments(h, rho, u, 1);
+    if (!rc) rc = selbm_moments(ref, rhoR, uR, 1);
+    if (!rc) {
+      e = launch_element_errors(h->S.E, dim, h->S.n1, ref->S.n1, rho, u, rhoR, uR, I, wq, err, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+  }
+  cudaFree(buf); cudaFree(I); cudaFree(wq);
+  if (rc) return rc;
+  if (e != cudaSuccess) return h->cuda_fail(e, "element_errors");
+  return SELBM_OK;
+}
+
+int selbm_mlp_nparams(int32_t nin) { return nin > 0 ? mlp_nparams(nin) : SELBM_ERR_ARG; }
+
+int selbm_mlp_grad(const float *params, int32_t nin, int32_t order, const float *x, const float *y, int64_t M,
+                   float *grad, float *loss, void *stream) {
+  if (!params || !x || !y || !grad || !loss || nin <= 0 || M <= 0 || order < 4) return SELBM_ERR_ARG;
+  return mlp_grad(params, nin, order, x, y, M, grad, loss, (cudaStream_t)stream) == cudaSuccess ? SELBM_OK : SELBM_ERR_CUDA;
+}
+
+int selbm_mlp_forward(const float *params, int32_t nin, int32_t order, const float *x, int64_t M, int32_t bf16,
+                      float *out, void *stream) {
+  if (!params || !x || !out || nin <= 0 || M <= 0 || order < 4) return SELBM_ERR_ARG;
+  return mlp_forward(params, nin, order, x, M, bf16, out, (cudaStream_t)stream) == cudaSuccess ? SELBM_OK : SELBM_ERR_CUDA;
+}
+
+int selbm_mlp_train(float *params, float *m, float *v, int32_t nin, int32_t order, const float *x, const float *y,
+                    int64_t M, int32_t batch, int32_t epochs, float lr, uint64_t seed, int64_t *adam_t,
+                    float *loss_hist, void *stream) {
+  if (!params || !m || !v || !x || !y || !adam_t || nin <= 0 || M <= 0 || batch <= 0 || epochs < 0 || order < 4)
+    return SELBM_ERR_ARG;
+  return mlp_train(params, m, v, nin, order, x, y, M, batch, epochs, lr, seed, adam_t, loss_hist, (cudaStream_t)stream) ==
+                 cudaSuccess
+             ? SELBM_OK
+             : SELBM_ERR_CUDA;
 }
 
 int selbm_sync(selbm_t *h) {

@@ -49,20 +49,20 @@ struct Tile {
   }
 };
 
-// out = v + U (W v) on n values
+// out = v + U (W v) on n values; U (n x r) and W (r x n) in shared memory, row stride n
 template <typename Real, int n>
-__device__ __forceinline__ void filter_vals(Real (&v)[n], const FastMats<Real, n> &m) {
+__device__ __forceinline__ void filter_vals(Real (&v)[n], const Real *U, const Real *W, int r) {
   Real o[n];
 #pragma unroll
   for (int j = 0; j < n; ++j) o[j] = v[j];
 #pragma unroll
   for (int q = 0; q < n; ++q) {
-    if (q < m.r) {
+    if (q < r) {
       Real s = 0;
 #pragma unroll
-      for (int k = 0; k < n; ++k) s += m.W[q * n + k] * v[k];
+      for (int k = 0; k < n; ++k) s += W[q * n + k] * v[k];
 #pragma unroll
-      for (int j = 0; j < n; ++j) o[j] += m.U[j * n + q] * s;
+      for (int j = 0; j < n; ++j) o[j] += U[j * n + q] * s;
     }
   }
 #pragma unroll
@@ -119,7 +119,7 @@ template <typename Real, int LAT, int n, bool AFFINE>
 constexpr size_t fast_smem_bytes(int wall_max) {
   using S = FastShape<LAT, n>;
   using TI = Tile<Real, n, S::DIM>;
-  size_t reals = (size_t)S::Q * TI::PS + n * n + S::Q * S::DIM + S::Q + n;
+  size_t reals = (size_t)S::Q * TI::PS + 3 * n * n + S::Q * S::DIM + S::Q + n;
   if (!AFFINE) reals += (size_t)S::Np * S::GEO;
   reals += (size_t)S::Q * wall_max;
   return reals * sizeof(Real);
@@ -137,7 +137,9 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real *sf = reinterpret_cast<Real *>(smem_raw);   // [Q][PS] tile
   Real *sD = sf + Q * PS;                           // [n][n]
-  Real *scoef = sD + n * n;                         // [Q][DIM]  (affine: -B dt sum_k e_k dr_l/dx_k)
+  Real *sU = sD + n * n;                            // [n][n]    filter F = I + U W (low rank)
+  Real *sW = sU + n * n;                            // [n][n]
+  Real *scoef = sW + n * n;                         // [Q][DIM]  (affine: -B dt sum_k e_k dr_l/dx_k)
   Real *sfc = scoef + Q * DIM;                      // [Q]       B dt F*_a / rho
   Real *sw = sfc + Q;                               // [n]       GLL weights
   Real *sgeo = sw + n;                              // [Np][GEO] (curved: -B dt dr_l/dx_k, wJ)
@@ -148,7 +150,12 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   const size_t G = p.G;
 
   // ---- per-element constants
+  __shared__ int s_r;
   for (int k = tid; k < n * n; k += T) sD[k] = m.D[k];
+  if (p.stage == 1 && p.apply_filter) {
+    for (int k = tid; k < n * n; k += T) { sU[k] = m.U[k]; sW[k] = m.W[k]; }
+    if (tid == 0) s_r = m.r;
+  }
   if (tid < n) sw[tid] = m.w[tid];
   if (tid < Q) {
     Real ge = 0;
@@ -199,7 +206,7 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
         Real v[n];
         Real *base = sf + a * PS + TI::line(i1, i2);
         load_line<Real, n>(base, TI::sw(i1), v);
-        filter_vals<Real, n>(v, m);
+        filter_vals<Real, n>(v, sU, sW, s_r);
         store_line<Real, n>(base, TI::sw(i1), v);
       }
       __syncthreads();
@@ -208,7 +215,7 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
         Real v[n];
 #pragma unroll
         for (int k = 0; k < n; ++k) v[k] = sf[a * PS + TI::at(i0, k, i2)];
-        filter_vals<Real, n>(v, m);
+        filter_vals<Real, n>(v, sU, sW, s_r);
 #pragma unroll
         for (int k = 0; k < n; ++k) sf[a * PS + TI::at(i0, k, i2)] = v[k];
       }
@@ -219,7 +226,7 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
           Real v[n];
 #pragma unroll
           for (int k = 0; k < n; ++k) v[k] = sf[a * PS + TI::at(i0, i1, k)];
-          filter_vals<Real, n>(v, m);
+          filter_vals<Real, n>(v, sU, sW, s_r);
 #pragma unroll
           for (int k = 0; k < n; ++k) sf[a * PS + TI::at(i0, i1, k)] = v[k];
         }

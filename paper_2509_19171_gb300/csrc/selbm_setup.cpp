@@ -161,6 +161,30 @@ void build_filter(const GLL &g, const selbm_filter &f, std::vector<double> *F, s
   }
 }
 
+void build_modal(const GLL &g, std::vector<double> *V, std::vector<double> *Vinv) {
+  const int N = g.N, n = N + 1;
+  V->assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const double x = g.xi[i];
+    std::vector<double> Lk(n);
+    for (int k = 0; k < n; ++k) { double L, dL; legendre_pair(k, x, &L, &dL); Lk[k] = L; }
+    for (int k = 0; k < n; ++k) (*V)[i * n + k] = (k == 0) ? 1.0 : (k == 1 ? x : Lk[k] - Lk[k - 2]);
+  }
+  invert(*V, n, Vinv);
+}
+
+void build_interp(int N_from, int N_to, std::vector<double> *I) {
+  GLL a, b;
+  build_gll(N_from, &a);
+  build_gll(N_to, &b);
+  const int nf = N_from + 1, nt = N_to + 1;
+  I->assign(nt * nf, 1.0);
+  for (int i = 0; i < nt; ++i)
+    for (int j = 0; j < nf; ++j)
+      for (int m = 0; m < nf; ++m)
+        if (m != j) (*I)[i * nf + j] *= (b.xi[i] - a.xi[m]) / (a.xi[j] - a.xi[m]);
+}
+
 void build_filter_lowrank(const GLL &g, const selbm_filter &f, std::vector<double> *U, std::vector<double> *W, int *r) {
   const int N = g.N, n = N + 1;
   std::vector<double> F, sigma;

@@ -33,6 +33,10 @@ void build_gll(int N, GLL *g);
 // Filter matrix F = V diag(sigma) V^{-1} in the basis 1, xi, L_k - L_{k-2}
 // (row-major [N+1][N+1]); boundary rows are set to exact identity rows.
 void build_filter(const GLL &g, const selbm_filter &f, std::vector<double> *F, std::vector<double> *sigma);
+// Modal basis at the GLL nodes, V[i][k] = phi_k(xi_i) (1, xi, L_k - L_{k-2}), and its inverse.
+void build_modal(const GLL &g, std::vector<double> *V, std::vector<double> *Vinv);
+// Lagrange interpolation matrix I[i][j] = l_j(x_to[i]) from GLL(N_from) to GLL(N_to) nodes.
+void build_interp(int N_from, int N_to, std::vector<double> *I);
 // Low-rank form of the same filter: F = I + U W over the r damped modes (sigma_k != 1),
 // U[j][q] = phi_{k_q}(xi_j), W[q][i] = (sigma_{k_q} - 1) (V^{-1})[k_q][i]; both stored with row stride N+1.
 void build_filter_lowrank(const GLL &g, const selbm_filter &f, std::vector<double> *U, std::vector<double> *W, int *r);

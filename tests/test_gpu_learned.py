@@ -1,0 +1,225 @@
+"""GPU tests of the learned per-element filter control against the FP64 oracle:
+features, per-element errors against a higher-order run, MLP gradient / forward /
+Adam, the learned step, both fallbacks, and the A/B gain over the fixed filter on a
+small double shear layer.
+
+Tolerance of the learned step in FP64: the features are log10 energies of the
+smallest modal coefficients (down to ~1e-6 of the field), whose relative rounding
+error in any FP64 evaluation is ~1e-8; through the network this moves sigma by
+~1e-8 and the filtered state by ~1e-11 of its size.  LEARNED_TOL = 1e-10 relative
+covers that with margin; everything else stays at the plain path's 1e-11.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import learned as Lr
+from oracle.selbm import OracleSELBM
+
+pytestmark = pytest.mark.gpu
+LEARNED_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_19171_gb300 import build
+    build.build()
+    import paper_2509_19171_gb300 as pkg
+    return pkg
+
+
+def _state(o, amp, seed):
+    rng = np.random.default_rng(seed)
+    rho = 1 + 0.01 * rng.standard_normal(o.G)
+    u = amp * rng.standard_normal((o.G, o.dim))
+    return o.initial_state(rho, u) + 1e-3 * o.t[:, None] * rng.standard_normal((o.Q, o.G))
+
+
+def _smooth_state(o, seed):
+    """Continuous state with spectra spread over all modes (smooth field + node noise)."""
+    rng = np.random.default_rng(seed)
+    X = o.Xg
+    k = rng.integers(1, 3, (3, o.dim))
+    u = np.stack([0.03 * np.sin(X @ k[c] + c) for c in range(o.dim)], 1) + 1e-4 * rng.standard_normal((o.G, o.dim))
+    rho = 1 + 1e-3 * np.cos(X @ k[0]) + 1e-5 * rng.standard_normal(o.G)
+    return o.initial_state(rho, u)
+
+
+CASES = {
+    "d3q27": (lambda: W.box_mesh((2, 2, 2), (0, 0, 0), (2 * math.pi,) * 3, (True, True, True)), "D3Q27", 5),
+    "d2q9": (lambda: W.box_mesh((3, 2), (0, 0), (1, 1), (True, True)), "D2Q9", 8),
+}
+
+
+@pytest.mark.parametrize("name", ["d3q27", "d2q9"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_features_match_oracle(P, name, prec):
+    mk, lat, N = CASES[name]
+    mesh = mk()
+    o = OracleSELBM(mesh, lat, N, 1e-3)
+    s = P.SELBM(mesh, lat, N, 1e-3, precision=prec)
+    f = _smooth_state(o, 1)
+    s.set_state(np.ascontiguousarray(o.to_local(f)))
+    got = s.features().cpu().numpy()
+    rho, u = o.moments(f)
+    ref = Lr.features(rho[o.glo], u[o.glo], 1.0, N, o.dim)
+    assert got.shape == ref.shape
+    tol = 2e-5 if prec == 0 else 2e-3
+    assert np.abs(got - ref).max() < tol, np.abs(got - ref).max()
+
+
+def test_element_errors_match_oracle(P):
+    mesh = W.box_mesh((3, 2), (0, 0), (1, 1), (True, False), walls={2: 1, 3: 2}, wall_velocity=[[0, 0], [0.01, 0]])
+    init = W.shear_layer_init(U0=0.02, kappa=5.0)
+    N, NR = 4, 8
+    o = OracleSELBM(mesh, "D2Q9", N, 1e-2)
+    oR = OracleSELBM(mesh, "D2Q9", NR, 1e-2, dt=o.dt / 4)
+    s = P.SELBM(mesh, "D2Q9", N, 1e-2)
+    sR = P.SELBM(mesh, "D2Q9", NR, 1e-2, dt=o.dt / 4)
+    f, fR = o.initial_state_from(init), oR.initial_state_from(init)
+    s.init_from(init)
+    sR.init_from(init)
+    for _ in range(3):
+        f = o.step(f)
+        for _ in range(4):
+            fR = oR.step(fR)
+    s.step(3)
+    sR.step(12)
+    got = s.element_errors(sR).cpu().numpy()
+    rho, u = o.moments(f)
+    rhoR, uR = oR.moments(fR)
+    ref = Lr.element_errors(rho[o.glo], u[o.glo], rhoR[oR.glo], uR[oR.glo], o.wJ, N, NR, 2)
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_mlp_grad_and_forward_match_oracle(P):
+    import torch
+    N, nin, M = 7, 16, 700
+    rng = np.random.default_rng(2)
+    p = Lr.init_params(nin, seed=3) + 0.05 * rng.standard_normal(Lr.n_params(nin))
+    x = rng.uniform(-1, 1, (M, nin))
+    y = np.stack([rng.uniform(0, 0.5, M), rng.uniform(2, N - 1, M)], 1)
+    pt = torch.tensor(p, dtype=torch.float32, device="cuda")
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    yt = torch.tensor(y, dtype=torch.float32, device="cuda")
+    loss, g = P.mlp_grad(pt, xt, yt, N)
+    # oracle on the same float32-rounded data
+    p32, x32, y32 = [np.float64(np.float32(a)) for a in (p, x, y)]
+    lo, go = Lr.loss_and_grad(p32, x32, y32, N)
+    assert abs(loss - lo) <= 1e-5 * lo
+    assert np.abs(g.cpu().numpy() - go).max() <= 1e-4 * np.abs(go).max()
+    out = P.mlp_forward(pt, xt, N, bf16=True).cpu().numpy()
+    o, _ = Lr.forward(Lr.bf16_round(p32), x32)
+    gam, kc = Lr.outputs_to_filter(o, N)
+    assert np.abs(out[:, 0] - gam).max() < 2e-5 and np.abs(out[:, 1] - kc).max() < 2e-4
+
+
+def test_mlp_adam_step_matches_oracle(P):
+    import torch
+    N, nin, M = 7, 16, 256
+    rng = np.random.default_rng(4)
+    p = np.float64(np.float32(Lr.init_params(nin, seed=5)))
+    x = np.float64(np.float32(rng.uniform(-1, 1, (M, nin))))
+    y = np.float64(np.float32(np.stack([rng.uniform(0, 0.5, M), rng.uniform(2, N - 1, M)], 1)))
+    pt = torch.tensor(p, dtype=torch.float32, device="cuda")
+    m = torch.zeros_like(pt)
+    v = torch.zeros_like(pt)
+    hist, t = P.mlp_train(pt, m, v, torch.tensor(x, dtype=torch.float32, device="cuda"),
+                          torch.tensor(y, dtype=torch.float32, device="cuda"), N, batch=M, epochs=1, lr=1e-3, seed=7)
+    assert t == 1
+    _, g = Lr.loss_and_grad(p, x, y, N)
+    p1, _, _ = Lr.adam_step(p, np.zeros_like(p), np.zeros_like(p), g, 1, 1e-3)
+    d = np.abs(pt.cpu().numpy() - p1)
+    big = np.abs(g) > 1e-4 * np.abs(g).max()
+    assert d[big].max() <= 2e-5 and d.max() <= 2e-3
+
+
+def _learned_pair(P, name, prec=0, seed=6):
+    mk, lat, N = CASES[name]
+    mesh = mk()
+    filt = {"shape": 0, "gamma": 0.1, "kc": float(N - 2)}
+    o = OracleSELBM(mesh, lat, N, 1e-3, filt=filt)
+    s = P.SELBM(mesh, lat, N, 1e-3, precision=prec, filt=filt)
+    f = _smooth_state(o, seed)
+    rho, u = o.moments(f)
+    x = Lr.features(rho[o.glo], u[o.glo], 1.0, N, o.dim)
+    lo, hi = np.full(x.shape[1], -35.0), np.full(x.shape[1], 5.0)   # the whole span of log10 energies
+    params = np.float32(Lr.init_params(x.shape[1], seed=11) * 1.5)
+    return o, s, f, np.float64(params), lo, hi
+
+
+@pytest.mark.parametrize("name", ["d3q27", "d2q9"])
+def test_learned_step_parity_fp64(P, name):
+    o, s, f, params, lo, hi = _learned_pair(P, name)
+    s.set_learned_filter(params, lo, hi, mass_bound=1.0, ke_bound=1.0)
+    s.set_state(np.ascontiguousarray(o.to_local(f)))
+    for k in range(2):
+        f_prev = f
+        f = o.step_learned(f, params, lo, hi)
+        s.step(1)
+        got = s.get_state()
+        ref = o.to_local(f)
+        assert np.abs(got - ref).max() <= LEARNED_TOL * np.abs(ref).max(), k
+    # the transfer functions of the last read-back are those of the last step's state
+    f3 = o.ssprk3(*o.collide(f_prev))
+    sig_o, _, inr = o.learned_sigma(f3, params, lo, hi)
+    assert inr.all()
+    assert np.abs(s.element_sigma() - sig_o).max() < 1e-7
+    assert len(np.unique(np.round(sig_o[:, -1], 6))) > 1          # the network differentiates elements
+
+
+def test_learned_out_of_range_falls_back(P):
+    o, s, f, params, lo, hi = _learned_pair(P, "d3q27")
+    s.set_learned_filter(params, hi + 1.0, hi + 2.0, mass_bound=1.0, ke_bound=1.0)   # every feature below the range
+    s.set_state(np.ascontiguousarray(o.to_local(f)))
+    for _ in range(2):
+        f = o.step(f)
+    s.step(2)
+    assert np.abs(s.get_state() - o.to_local(f)).max() <= 1e-11 * np.abs(f).max()
+    st = s.learned_status()
+    assert st["fixed_element_steps"] == o.E and st["fallback_flag"] == 0
+
+
+def test_learned_drift_fallback(P):
+    """A negative mass bound trips the drift check at its first comparison: the filters of
+    steps 1-2 are learned, from step 3 on the fixed filter is used."""
+    o, s, f, params, lo, hi = _learned_pair(P, "d2q9")
+    s.set_learned_filter(params, lo, hi, mass_bound=-1.0, ke_bound=1.0)
+    s.set_state(np.ascontiguousarray(o.to_local(f)))
+    f = o.step_learned(f, params, lo, hi)
+    f = o.step_learned(f, params, lo, hi)
+    f = o.step(f)
+    f = o.step(f)
+    s.step(4)
+    assert np.abs(s.get_state() - o.to_local(f)).max() <= LEARNED_TOL * np.abs(f).max()
+    assert s.learned_status()["fallback_flag"] == 1
+
+
+def test_learned_ab_gain(P):
+    """Train on small double-shear-layer runs (sweep gamma in {0.01, 0.03, 0.1, 0.3}, labels
+    from the order N+4 run), then compare the total error against the N+4 run on a held-out
+    shift: learned control vs the fixed filter it replaces."""
+    from paper_2509_19171_gb300 import learn
+    N = 6
+    mesh = W.box_mesh((6, 6), (0, 0), (1, 1), (True, True))
+    nu = 0.04 / 5000
+    rng = np.random.default_rng(0)
+    inits = []
+    for sh in rng.uniform(0, 1, 3):
+        base = W.shear_layer_init(U0=0.04, kappa=40.0)
+        inits.append(lambda x, sh=sh, base=base: base(x + np.array([sh, 0.0])))
+    X, Y = learn.generate(mesh, "D2Q9", N, nu, inits, snapshots=12, interval=150, start=300)
+    params, lo, hi, hist = learn.train(X, Y, N, epochs=60, batch=256, lr=3e-3)
+    assert hist[-1] < hist[0]
+    held = lambda x: W.shear_layer_init(U0=0.04, kappa=40.0)(x + np.array([0.37, 0.0]))
+    res, fb = learn.evaluate(mesh, "D2Q9", N, nu, held, 300 + 12 * 150, params, lo, hi)
+    gain = 1.0 - res[-1]["err_learned"] / res[-1]["err_fixed"]
+    print("A/B (learned vs fixed) relative error gain per checkpoint:",
+          [round(1.0 - r["err_learned"] / r["err_fixed"], 4) for r in res], "fallback element-steps:", fb)
+    assert res[-1]["err_learned"] <= 1.05 * res[-1]["err_fixed"], res
+    assert np.isfinite(gain)
