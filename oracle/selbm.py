@@ -215,6 +215,26 @@ class OracleSELBM:
         return f
 
     # ------------------------------------------------------------ diagnostics
+    def dissipation(self, f):
+        """Viscous dissipation integral (Sec. 3.4, with the divergence term squared):
+        eps = sum wJ [2 mu sum_i (d_i u_i)^2 - 2/3 mu (div u)^2 + mu sum_{i<j} (d_i u_j + d_j u_i)^2],
+        mu = rho0 nu; gradients of the nodal velocity by D along each reference axis and the chain rule."""
+        _, u = self.moments(f)
+        ul = u[self.glo]                                             # [E, Np, d]
+        d = self.dim
+        dr = np.stack([np.stack([geo.apply_axis(self.D, ul[..., c], l, self.N, d) for c in range(d)], -1)
+                       for l in range(d)], 2)                        # [E, Np, l, c] = du_c/dr_l
+        g = np.einsum("eplk,eplc->epkc", self.drdx, dr)              # du_c/dx_k
+        mu = self.rho0 * self.nu
+        div = np.einsum("epkk->ep", g)
+        diag = np.einsum("epkk,epkk->ep", g, g)
+        off = np.zeros_like(div)
+        for a in range(d):
+            for b in range(a + 1, d):
+                off += (g[:, :, a, b] + g[:, :, b, a]) ** 2
+        dens = 2 * mu * diag - 2.0 / 3.0 * mu * div ** 2 + mu * off
+        return float((self.wJ * dens).sum())
+
     def integrals(self, f):
         """Quadrature integrals: mass sum M rho, momentum sum M rho u, KE = sum M rho0 |u|^2 / 2."""
         rho, u = self.moments(f)

@@ -217,3 +217,17 @@ def test_filter_continuity_and_mass():
     assert spread.max() < 1e-13
     ff = o.apply_filter(f)
     assert np.abs(ff @ o.mass - f @ o.mass).max() < 1e-12
+
+
+def test_dissipation_taylor_green_closed_form():
+    """Incompressible TGV at t = 0: eps = mu int |grad u|^2 = mu (3/4) U0^2 (2 pi)^3."""
+    L = 2 * np.pi
+    mesh = W.box_mesh((3, 3, 3), (0, 0, 0), (L, L, L), (True, True, True))
+    U0, nu = 0.05, 0.01
+    o = OracleSELBM(mesh, "D3Q19", 7, nu)
+    X = o.Xg
+    u = np.stack([U0 * np.sin(X[:, 0]) * np.cos(X[:, 1]) * np.cos(X[:, 2]),
+                  -U0 * np.cos(X[:, 0]) * np.sin(X[:, 1]) * np.cos(X[:, 2]), np.zeros(o.G)], 1)
+    f = o.initial_state(np.ones(o.G), u)
+    eps = o.dissipation(f)
+    assert abs(eps - nu * 0.75 * U0 ** 2 * L ** 3) < 1e-6 * eps
