@@ -4,9 +4,15 @@ Metric: GLL-node x population updates per second (local nodes, i.e. element
 copies of shared nodes counted once per element: E * (N+1)^d * Q per step).
 Default workload: 3D Taylor-Green vortex, D3Q27, 16^3 hex elements at N=7
 (2,097,152 local nodes, 56.6M populations), quadratic filter gamma=0.1,
-kc=N-2.  One step = collision, three SSPRK3 stages (element kernel +
-assembly kernel each), filter.  Inputs are larger than L2 (one FP64 state
-array = 303 MB), so no flush is needed between steps.
+kc=N-2.  One step = (learned filter control) + collision, three SSPRK3
+stages (element kernel + assembly kernel each), filter.  Inputs are larger
+than L2 (one FP32 state array = 152 MB, FP64 303 MB), so no flush is needed.
+
+Forms: fp64 (the paper's method in FP64), fp32dev (FP32 deviations), and the
+headline fp32dev_learned (FP32 deviations + learned per-element filter
+control with the fixed filter as fallback).  Each form is timed with
+captured-graph launches; per-kernel times come from a separate short run
+with the library's event timers.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank runs an independent replica (weak scaling).
@@ -147,44 +153,71 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- our arm
-def run_form(P, torch, case, precision, steps, warmup, dev_index):
-    s = P.from_case(case, precision=precision, stream=torch.cuda.current_stream().cuda_stream)
+WEIGHTS = os.path.join(ROOT, "paper_2509_19171_gb300", "weights", "learned_filter_tgv3d_n7_d3q27.npz")
+
+
+def make_form(P, torch, case, form):
+    prec = P.FP64 if form == "fp64" else P.FP32DEV
+    s = P.from_case(case, precision=prec, stream=torch.cuda.current_stream().cuda_stream)
     s.init_from(case.init)
-    s.step(warmup)
-    s.sync()
+    if form == "fp32dev_learned":
+        w = np.load(WEIGHTS)
+        s.set_learned_filter(w["params"], w["lo"], w["hi"], mass_bound=1e-6)
     return s
 
 
+def max_over_ranks(ms, dist, device):
+    """Largest per-rank time (ms) of the timed region, identical on every rank."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(updates_per_rank_step, steps, world, ms_max):
+    """Whole-job updates/s: all ranks' units over the slowest rank's time (weak scaling)."""
+    return updates_per_rank_step * steps * world / (ms_max * 1e-3)
+
+
 def time_steps(torch, s, steps, dist):
+    """CUDA-event time of `steps` steps on the launching stream (captured-graph launches)."""
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    s.timers(True)
     e0.record(st)
     s.step(steps)
     e1.record(st)
     torch.cuda.synchronize()
-    t = s.timers_read()
-    s.timers(False)
     if dist:
         dist.barrier()
-    return e0.elapsed_time(e1), t
+    return e0.elapsed_time(e1)
 
 
-def e2e_run(P, torch, case, precision, steps):
+def kernel_times(torch, s, steps):
+    """Per-kernel CUDA-event times of `steps` eager steps (library timers)."""
+    torch.cuda.synchronize()
+    s.timers(True)
+    s.step(steps)
+    t = s.timers_read()
+    s.timers(False)
+    return t
+
+
+def e2e_run(P, torch, case, form, steps):
     """Public-API end to end: initial fields H2D from pinned host, K steps, moments D2H to pinned host."""
-    s = P.from_case(case, precision=precision, stream=torch.cuda.current_stream().cuda_stream)
+    s = make_form(P, torch, case, form)
     x = s.node_coords().reshape(-1, s.dim)
     rho, u = case.init(x)
     rho_h = torch.from_numpy(np.ascontiguousarray(rho, np.float64)).pin_memory()
     u_h = torch.from_numpy(np.ascontiguousarray(u[:, : s.dim], np.float64)).pin_memory()
     rho_o = torch.empty_like(rho_h).pin_memory()
     u_o = torch.empty_like(u_h).pin_memory()
-    # warm-up of the same sequence
     s.init(rho_h, u_h)
-    s.step(2)
+    s.step(3)
     s.moments(rho_o, u_o)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -238,7 +271,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "pipe", "shear"])
-    ap.add_argument("--forms", default="fp64,fp32dev")
+    ap.add_argument("--forms", default="fp64,fp32dev,fp32dev_learned")
     ap.add_argument("--n", type=int, default=16, help="TGV elements per side")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and clock sampling")
     args = ap.parse_args()
@@ -291,73 +324,100 @@ def main():
     hbm = float(pk["hbm_gbs"])
 
     forms = [f for f in args.forms.split(",") if f]
-    results = {}
-    clocks = None
-    for form in forms:
-        prec = P.FP64 if form == "fp64" else P.FP32DEV
+    if "fp32dev_learned" in forms and not os.path.exists(WEIGHTS):
+        forms.remove("fp32dev_learned")
+    main_form = "fp32dev_learned" if "fp32dev_learned" in forms else forms[-1]
+    order = [f for f in forms if f != main_form] + [main_form]
+    results, fields, clocks = {}, {}, None
+    ksteps = min(args.steps, 5)
+    for form in order:
         rsz = 8 if form == "fp64" else 4
-        s = run_form(P, torch, case, prec, args.steps, args.warmup, dev_index)
-        sampler = ClockSampler() if (not args.no_extras and form == forms[0]) else None
+        s = make_form(P, torch, case, form)
+        s.step(args.warmup)
+        s.sync()
+        sampler = ClockSampler() if (not args.no_extras and form == main_form) else None
         if sampler:
             sampler.start()
-        ms, t = time_steps(torch, s, args.steps, dist)
+        ms = time_steps(torch, s, args.steps, dist)
         if sampler:
             clocks = sampler.stop(dev_index)
-        if dist:
-            tt = torch.tensor([ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(ms, dist, "cuda")
+        t = kernel_times(torch, s, ksteps)
         e, _, _ = s.lattice_table()
         nz_axes = float(np.abs(e).astype(bool).sum(1).mean()) if info["affine"] else float(case.mesh.dim)
         Q = s.Q
         upd_step = case.mesh.nelem * info["Np"] * Q
-        value = upd_step * args.steps * world / (ms * 1e-3)
+        value = job_throughput(upd_step, args.steps, world, ms)
         s1, s23, a1, a23 = bytes_per_step(c, Q, rsz, info["affine"])
         f1, f23 = flops_per_step(case, nz_axes, Q)
         st1_ms = t["stage1"][0] / max(t["stage1"][1], 1)
         st23_ms = t["stage23"][0] / max(t["stage23"][1], 1)
         as_ms = t["assembly"][0] / max(t["assembly"][1], 1)
+        lc_ms = t["other"][0] / max(t["other"][1], 1)
         stage_ms = (t["stage1"][0] + t["stage23"][0]) / max(t["stage1"][1] + t["stage23"][1], 1)
         stage_bytes = (s1 + 2 * s23) / 3
         stage_flops = (f1 + 2 * f23) / 3
         step_bytes = s1 + 2 * s23 + a1 + 2 * a23
-        results[form] = {
+        learned = form == "fp32dev_learned"
+        entry = {
             "value": value, "ms_per_step": ms / args.steps, "dtype": "f64" if form == "fp64" else "f32",
             "kernel_ms": {"stage1": st1_ms, "stage2_3": st23_ms, "assembly": as_ms},
-            "launches": {k: v[1] for k, v in t.items()},
+            "launches_per_step": 6 + (3 if learned else 0),
             "hbm_gbs_alg_step": step_bytes / (ms / args.steps * 1e-3) / 1e9,
             "stage_hbm_frac": stage_bytes / (stage_ms * 1e-3) / 1e9 / hbm,
             "stage_fp64_frac": (stage_flops / (stage_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS) if form == "fp64" else None,
             "stage_bytes": stage_bytes, "stage_flops": stage_flops, "stage_ms": stage_ms,
             "bytes_per_update": step_bytes / upd_step,
         }
+        if learned:
+            st = s.learned_status()
+            entry["kernel_ms"]["learned_control"] = lc_ms
+            entry["learned"] = {"fallback_flag": st["fallback_flag"],
+                                "fixed_element_steps": st["fixed_element_steps"],
+                                "weights": os.path.relpath(WEIGHTS, ROOT)}
+        rho, u = s.moments()
+        fields[form] = (rho, u)
+        results[form] = entry
         s.close()
         del s
         torch.cuda.empty_cache()
-
-    main_form = forms[0]
+    if "fp64" in fields:
+        r64, u64 = fields["fp64"]
+        for form in results:
+            if form == "fp64":
+                continue
+            r, u = fields[form]
+            du = np.linalg.norm(u - u64, axis=-1)
+            results[form]["err_vs_fp64"] = {
+                "after_steps": args.warmup + args.steps + ksteps,
+                "u_max_over_U0": float(du.max() / case.U0), "u_rms_over_U0": float(np.sqrt((du ** 2).mean()) / case.U0),
+                "rho_max": float(np.abs(r - r64).max()), "rho_rms": float(np.sqrt(((r - r64) ** 2).mean()))}
+        if main_form != "fp64":
+            results[main_form]["speedup_vs_fp64"] = results[main_form]["value"] / results["fp64"]["value"]
     r = results[main_form]
     if main_form == "fp64":
         achieved = r["stage_flops"] / (r["stage_ms"] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "stage_kernel (FP64 pipe)", "achieved": achieved,
+        roof = {"bound": "alu", "kernel": "stage_fast_kernel (FP64 pipe)", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe: 2.07/clk/SM)",
                 "traffic": None, "hbm_frac_alg": r["stage_hbm_frac"]}
     else:
         achieved = r["stage_bytes"] / (r["stage_ms"] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": "stage_kernel", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_source": f"{pk_kind} hbm_gbs", "traffic": None}
+        roof = {"bound": "hbm", "kernel": "stage_fast_kernel<float, D3Q27, N=7>", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "peak_source": f"{pk_kind} hbm_gbs (of {pk_kind})",
+                "traffic": None}
 
     line = {"metric": metric, "value": r["value"], "unit": "node-pop updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": r["dtype"],
             "data": "synthetic",
             "config": workload_config(case, main_form, world),
-            "roofline": roof, "forms": results, "gpu_launches": int(sum(results[main_form]["launches"].values()))}
+            "roofline": roof, "forms": results,
+            "gpu_launches": int(results[main_form]["launches_per_step"] * args.steps)}
     if clocks:
         line["clocks"] = clocks
     if rank == 0 and not args.no_extras:
-        ms_e2e, h2d, d2h = e2e_run(P, torch, case, P.FP64 if main_form == "fp64" else P.FP32DEV, args.steps)
+        ms_e2e, h2d, d2h = e2e_run(P, torch, case, main_form, args.steps)
         upd = case.mesh.nelem * info["Np"] * info["Q"] * args.steps
         line["e2e"] = {"value": upd / (ms_e2e * 1e-3), "unit": "node-pop updates/s",
                        "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,

@@ -155,7 +155,10 @@ int selbm_set_body_force(selbm_t *h, const double g[3]);
 /*
  * Diagnostics of the current (filtered) state, FP64 quadrature sums:
  * out[0] mass = sum_g M_g rho, out[1..3] momentum sum M rho u,
- * out[4] kinetic energy sum M rho0 |u|^2 / 2, out[5] 0 (reserved), out[6] dt, out[7] time.
+ * out[4] kinetic energy sum M rho0 |u|^2 / 2, out[5] viscous dissipation integral
+ * eps = 2 mu sum_i (d_i u_i)^2 - (2/3) mu (div u)^2 + mu sum_{i<j} (d_i u_j + d_j u_i)^2
+ * (mu = rho0 nu; Sec. 3.4 with the square of the divergence term), quadrature over
+ * element-local nodes with GLL derivatives, out[6] dt, out[7] time.
  * Returns SELBM_ERR_NONFINITE if the state holds NaN/Inf.
  */
 int selbm_diagnostics(selbm_t *h, double out[8]);

@@ -44,7 +44,7 @@ struct selbm {
   double dt = 0, tau = 0, lam = 0, omega = 0, time = 0;
   int64_t steps = 0;
   bool initialized = false, filter_pending = false, filter_on = false, has_force = false;
-  bool use_fast = true;
+  bool use_fast = true;   // SELBM_GENERIC_KERNEL=1 in the environment selects the generic stage kernel
   // learned per-element filter control
   bool learned = false;
   int nin = 0;
@@ -53,7 +53,19 @@ struct selbm {
   __nv_bfloat16 *d_W = nullptr;
   double *d_acc = nullptr;
   int *d_flag = nullptr, *d_nfb = nullptr;
-  int wall_max = 0;   // SELBM_GENERIC_KERNEL=1 in the environment selects the generic stage kernel
+  int wall_max = 0;
+  // captured steps (slot 0: no pending filter, slot 1: filter pending), launched with
+  // cudaGraphLaunch on the handle's stream
+  bool graph_enabled = true;   // SELBM_NO_GRAPH=1 in the environment disables capture
+  int64_t eager_steps[2] = {0, 0};
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  cudaStream_t cap_stream = nullptr;
+  void invalidate_graph() {
+    for (int k = 0; k < 2; ++k) {
+      if (gexec[k]) cudaGraphExecDestroy(gexec[k]);
+      gexec[k] = nullptr;
+    }
+  }
   std::string err;
   std::vector<double> Fmat, sigma, FU, FW;
   int Fr = 0;
@@ -61,7 +73,7 @@ struct selbm {
   void *FA = nullptr, *F0 = nullptr, *F2 = nullptr, *T = nullptr, *RHO = nullptr, *BUF = nullptr;
   void *d_el_drdx = nullptr, *d_el_J = nullptr, *d_drdx = nullptr, *d_wJ = nullptr, *d_gllw = nullptr;
   void *d_D = nullptr, *d_F = nullptr, *d_wall_u = nullptr, *d_walls = nullptr, *d_minv = nullptr;
-  int32_t *d_l2g = nullptr, *d_bslot = nullptr, *d_binv = nullptr, *d_bnode_g = nullptr, *d_bnode_off = nullptr, *d_bnode_slot = nullptr;
+  int32_t *d_l2g = nullptr, *d_bslot = nullptr, *d_bnode_g = nullptr, *d_bnode_off = nullptr, *d_bnode_slot = nullptr;
   int32_t *d_wall_off = nullptr, *d_first = nullptr;
   uint8_t *d_owner = nullptr;
   double *d_mass = nullptr, *d_partial = nullptr, *d_diag = nullptr;
@@ -197,7 +209,7 @@ KParams<Real> base_params(selbm *h) {
   for (int k = 0; k < 3; ++k) p.g[k] = (Real)(k < S.dim ? h->P.body_accel[k] : 0.0);
   p.has_force = h->has_force;
   p.wall_max = h->wall_max;
-  p.l2g = h->d_l2g; p.owner = h->d_owner; p.bslot = h->d_bslot; p.binv = h->d_binv;
+  p.l2g = h->d_l2g; p.owner = h->d_owner; p.bslot = h->d_bslot;
   p.el_drdx = (const Real *)h->d_el_drdx; p.el_J = (const Real *)h->d_el_J;
   p.drdx = (const Real *)h->d_drdx; p.wJ = (const Real *)h->d_wJ; p.gllw = (const Real *)h->d_gllw;
   p.Dm = (const Real *)h->d_D; p.Fm = (const Real *)h->d_F;
@@ -295,6 +307,7 @@ cudaError_t enqueue_finalize(selbm *h) {
 }
 
 int set_filter_internal(selbm *h, const selbm_filter &f) {
+  h->invalidate_graph();
   if (f.gamma != 0.0 && !(f.kc >= 1.0 && f.kc < h->S.N)) return h->fail(SELBM_ERR_ARG, "filter kc must satisfy 1 <= kc < N");
   if (f.gamma < 0.0 || f.gamma > 1.0) return h->fail(SELBM_ERR_ARG, "filter gamma must be in [0, 1]");
   h->P.filter = f;
@@ -350,6 +363,8 @@ int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_
   {
     const char *gk = std::getenv("SELBM_GENERIC_KERNEL");
     h->use_fast = !(gk && gk[0] == '1');
+    const char *ng = std::getenv("SELBM_NO_GRAPH");
+    h->graph_enabled = !(ng && ng[0] == '1');
   }
   std::string err;
   int rc = build_setup(*mesh, params->lattice, params->order, &h->S, &err);
@@ -370,12 +385,6 @@ int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_
   CK(upload(&h->d_l2g, S.l2g));
   CK(upload(&h->d_owner, S.owner));
   CK(upload(&h->d_bslot, S.bslot));
-  {
-    std::vector<int32_t> binv(std::max(S.Nb, 1), 0);
-    for (int i = 0; i < S.Np; ++i)
-      if (S.bslot[i] >= 0) binv[S.bslot[i]] = i;
-    CK(upload(&h->d_binv, binv));
-  }
   CK(upload(&h->d_bnode_g, S.bnode_g));
   CK(upload(&h->d_bnode_off, S.bnode_off));
   CK(upload(&h->d_bnode_slot, S.bnode_slot));
@@ -383,6 +392,7 @@ int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_
   CK(upload(&h->d_mass, S.mass));
   CK(cudaMalloc((void **)&h->d_partial, diag_blocks() * 6 * sizeof(double)));
   CK(cudaMalloc((void **)&h->d_diag, 8 * sizeof(double)));
+  CK(cudaMemset(h->d_diag, 0, 8 * sizeof(double)));
   if (h->prec == SELBM_FP64) CK(upload_real<double>(h)); else CK(upload_real<float>(h));
 #undef CK
   rc = set_filter_internal(h, params->filter);
@@ -394,10 +404,12 @@ int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_
 void selbm_destroy(selbm_t *h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  h->invalidate_graph();
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (auto &u : h->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   for (void *p : h->allocs) cudaFree(p);
-  void *own[] = {h->d_l2g, h->d_owner, h->d_bslot, h->d_binv, h->d_bnode_g, h->d_bnode_off, h->d_bnode_slot, h->d_first,
+  void *own[] = {h->d_l2g, h->d_owner, h->d_bslot, h->d_bnode_g, h->d_bnode_off, h->d_bnode_slot, h->d_first,
                  h->d_mass, h->d_partial, h->d_diag, h->d_io};
   for (void *p : own)
     if (p) cudaFree(p);
@@ -500,13 +512,49 @@ int selbm_get_state(selbm_t *h, double *f, int on_device) {
   return SELBM_OK;
 }
 
+// capture one step of the given variant into a graph (after one eager step of that
+// variant has set the kernels' attributes); any failure leaves the handle on eager launches
+static void build_step_graph(selbm *h, int slot) {
+  if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    h->graph_enabled = false;
+    return;
+  }
+  cudaGraph_t g = nullptr;
+  cudaStream_t user = h->stream;
+  h->stream = h->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  cudaError_t e2 = cudaSuccess;
+  if (e == cudaSuccess) {
+    e2 = h->prec == SELBM_FP64 ? enqueue_step<double>(h, slot == 1) : enqueue_step<float>(h, slot == 1);
+    e = cudaStreamEndCapture(h->cap_stream, &g);
+  }
+  h->stream = user;
+  if (e == cudaSuccess && e2 == cudaSuccess && g) e = cudaGraphInstantiate(&h->gexec[slot], g, 0);
+  else e = cudaErrorUnknown;
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->gexec[slot] = nullptr;
+    h->graph_enabled = false;
+    cudaGetLastError();
+  }
+}
+
 int selbm_step(selbm_t *h, int64_t nsteps) {
   if (!h) return SELBM_ERR_ARG;
   if (!h->initialized) return h->fail(SELBM_ERR_STATE, "state not initialised");
   if (nsteps < 0) return h->fail(SELBM_ERR_ARG, "nsteps < 0");
   for (int64_t k = 0; k < nsteps; ++k) {
     const bool filt = h->filter_pending && (h->filter_on || h->learned);
-    cudaError_t e = h->prec == SELBM_FP64 ? enqueue_step<double>(h, filt) : enqueue_step<float>(h, filt);
+    const int slot = filt ? 1 : 0;
+    cudaError_t e = cudaSuccess;
+    const bool graphable = h->graph_enabled && !h->timing;
+    if (graphable && !h->gexec[slot] && h->eager_steps[slot] > 0) build_step_graph(h, slot);
+    if (graphable && h->gexec[slot]) {
+      e = cudaGraphLaunch(h->gexec[slot], h->stream);
+    } else {
+      e = h->prec == SELBM_FP64 ? enqueue_step<double>(h, filt) : enqueue_step<float>(h, filt);
+      h->eager_steps[slot]++;
+    }
     if (e != cudaSuccess) return h->cuda_fail(e, "step");
     h->filter_pending = true;
     h->steps++;
@@ -556,6 +604,7 @@ int selbm_set_body_force(selbm_t *h, const double g[3]) {
   if (!h || !g) return SELBM_ERR_ARG;
   for (int k = 0; k < 3; ++k) h->P.body_accel[k] = g[k];
   h->has_force = g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0;
+  h->invalidate_graph();
   return SELBM_OK;
 }
 
@@ -567,13 +616,33 @@ int selbm_diagnostics(selbm_t *h, double out[8]) {
   cudaError_t e = h->prec == SELBM_FP64
                       ? launch_diag<double>(h->lat, (const double *)h->BUF, h->d_mass, h->S.G, h->P.rho0, h->d_partial, h->d_diag, h->stream)
                       : launch_diag<float>(h->lat, (const float *)h->BUF, h->d_mass, h->S.G, h->P.rho0, h->d_partial, h->d_diag, h->stream);
-  double tmp[6];
-  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, h->d_diag, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  // dissipation: velocity at local nodes, then per-element gradient integrals
+  const size_t nl = h->nloc(), dim = h->S.dim;
+  double *d_eps = nullptr;
+  if (e == cudaSuccess && ensure_io(h, nl * (1 + dim) * 8 + (h->S.E + 1) * 8) != SELBM_OK) e = cudaErrorMemoryAllocation;
+  if (e == cudaSuccess) {
+    double *rho_l = h->d_io, *u_l = h->d_io + nl, *part = h->d_io + nl * (1 + dim);
+    d_eps = h->d_diag + 6;
+    const double mu = h->P.rho0 * h->P.nu;
+    e = h->prec == SELBM_FP64
+            ? launch_moments<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, rho_l, u_l, h->stream)
+            : launch_moments<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, rho_l, u_l, h->stream);
+    if (e == cudaSuccess)
+      e = h->prec == SELBM_FP64
+              ? launch_eps<double>(u_l, (int)dim, h->S.n1, h->S.Np, h->S.E, h->S.affine, (const double *)h->d_el_drdx,
+                                   (const double *)h->d_drdx, (const double *)h->d_el_J, (const double *)h->d_wJ,
+                                   (const double *)h->d_gllw, (const double *)h->d_D, mu, part, d_eps, h->stream)
+              : launch_eps<float>(u_l, (int)dim, h->S.n1, h->S.Np, h->S.E, h->S.affine, (const float *)h->d_el_drdx,
+                                  (const float *)h->d_drdx, (const float *)h->d_el_J, (const float *)h->d_wJ,
+                                  (const float *)h->d_gllw, (const float *)h->d_D, mu, part, d_eps, h->stream);
+  }
+  double tmp[7];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, h->d_diag, 7 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "diagnostics");
   out[0] = tmp[0];
   for (int k = 0; k < 3; ++k) out[1 + k] = tmp[1 + k];
-  out[4] = tmp[4]; out[5] = 0.0; out[6] = h->dt; out[7] = h->time;
+  out[4] = tmp[4]; out[5] = tmp[6]; out[6] = h->dt; out[7] = h->time;
   if (tmp[5] > 0) return h->fail(SELBM_ERR_NONFINITE, "state holds non-finite values");
   return SELBM_OK;
 }
@@ -669,6 +738,7 @@ int selbm_set_learned_filter(selbm_t *h, const float *params, const float *lo, c
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_nfb, 0, 2 * sizeof(int), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "set_learned_filter");
+  h->invalidate_graph();
   h->nin = nin;
   h->mass_bound = mass_bound;
   h->ke_bound = ke_bound;
@@ -687,6 +757,7 @@ int selbm_clear_learned_filter(selbm_t *h) {
     h->filter_pending = false;
   }
   h->learned = false;
+  h->invalidate_graph();
   return SELBM_OK;
 }
 

@@ -328,16 +328,34 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   //      their results can replace those populations in the tile
   const Real Je = AFFINE ? p.el_J[e] : Real(0);
   constexpr int ROUNDS = (Q * NL + T - 1) / T;
+  // T is a multiple of NL, so this thread's r-line (i1, i2) is the same in every round:
+  // the offsets of the s-lines (k, i2) and t-lines (i1, k) it reads are fixed once here
+  // (for the swizzled tile they depend on k only through k & 3, plus an immediate)
+  const int L = tid % NL;
+  const int i1 = DIM == 3 ? L % n : L, i2 = DIM == 3 ? L / n : 0;
+  int yq[4], zq[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    yq[q] = TI::SW ? i2 * TI::PL + ((q ^ (i2 & 3)) << 3) : i2 * TI::PL;
+    zq[q] = TI::SW ? ((i1 ^ q) << 3) : i1 * n;
+  }
+  auto yline = [&](int k) -> int { return TI::SW ? yq[k & 3] + ((k & 4) << 3) : yq[0] + k * n; };
+  auto zline = [&](int k) -> int { return TI::SW ? k * TI::PL + zq[k & 3] : k * TI::PL + zq[0]; };
+  const int zswz = TI::sw(i1);
+  const Real *sDi1 = sD + i1 * n, *sDi2 = sD + i2 * n;
+  const Real wl = DIM == 3 ? sw[i1] * sw[i2] : sw[i1];
+  const Real Jwl = Je * wl;
+  const bool edge_line = i1 == 0 || i1 == n - 1 || (DIM == 3 && (i2 == 0 || i2 == n - 1));
+  const int own = TI::line(i1, i2), own_swz = TI::sw(i1);
   for (int rd = 0; rd < ROUNDS; ++rd) {
     const int t = rd * T + tid;
     const bool active = t < Q * NL;
-    const int a = active ? t / NL : 0, L = active ? t - a * NL : 0;
-    const int i1 = DIM == 3 ? L % n : L, i2 = DIM == 3 ? L / n : 0;
+    const int a = active ? t / NL : 0;
     Real res[n];
     if (active) {
       const Real *fa = sf + a * PS;
       Real v[n];
-      load_line<Real, n>(fa + TI::line(i1, i2), TI::sw(i1), v);
+      load_line<Real, n>(fa + own, own_swz, v);
       Real adv[n];
 #pragma unroll
       for (int j = 0; j < n; ++j) adv[j] = 0;
@@ -356,20 +374,19 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
         if (c1 != Real(0)) {
 #pragma unroll KU
           for (int k = 0; k < n; ++k) {
-            const Real s = c1 * sD[i1 * n + k];
+            const Real s = c1 * sDi1[k];
             Real w[n];
-            load_line<Real, n>(fa + TI::line(k, i2), TI::sw(k), w);
+            load_line<Real, n>(fa + yline(k), TI::sw(k), w);
 #pragma unroll
             for (int j = 0; j < n; ++j) adv[j] += s * w[j];
           }
         }
         if (DIM == 3 && c2 != Real(0)) {
-          const int swz = TI::sw(i1);
 #pragma unroll KU
           for (int k = 0; k < n; ++k) {
-            const Real s = c2 * sD[i2 * n + k];
+            const Real s = c2 * sDi2[k];
             Real w[n];
-            load_line<Real, n>(fa + TI::line(i1, k), swz, w);
+            load_line<Real, n>(fa + zline(k), zswz, w);
 #pragma unroll
             for (int j = 0; j < n; ++j) adv[j] += s * w[j];
           }
@@ -402,9 +419,9 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
           for (int j = 0; j < n; ++j) d[j] = 0;
 #pragma unroll KU
           for (int k = 0; k < n; ++k) {
-            const Real s = sD[i1 * n + k];
+            const Real s = sDi1[k];
             Real w[n];
-            load_line<Real, n>(fa + TI::line(k, i2), TI::sw(k), w);
+            load_line<Real, n>(fa + yline(k), TI::sw(k), w);
 #pragma unroll
             for (int j = 0; j < n; ++j) d[j] += s * w[j];
           }
@@ -415,12 +432,11 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
           Real d[n];
 #pragma unroll
           for (int j = 0; j < n; ++j) d[j] = 0;
-          const int swz = TI::sw(i1);
 #pragma unroll KU
           for (int k = 0; k < n; ++k) {
-            const Real s = sD[i2 * n + k];
+            const Real s = sDi2[k];
             Real w[n];
-            load_line<Real, n>(fa + TI::line(i1, k), swz, w);
+            load_line<Real, n>(fa + zline(k), zswz, w);
 #pragma unroll
             for (int j = 0; j < n; ++j) d[j] += s * w[j];
           }
@@ -430,24 +446,23 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
       }
       // element-interior nodes: B f^{s-1} + (-B dt) e.grad f  (A f^0 is added on output);
       // element-boundary nodes: weighted share wJ (-B dt) e.grad f for the assembly
-      const Real wl = DIM == 3 ? sw[i1] * sw[i2] : sw[i1];
-      const bool edge_line = i1 == 0 || i1 == n - 1 || (DIM == 3 && (i2 == 0 || i2 == n - 1));
 #pragma unroll
       for (int j = 0; j < n; ++j) {
         const bool bnd = edge_line || j == 0 || j == n - 1;
         if (!bnd) {
           res[j] = (p.stage == 1 ? v[j] : p.B * v[j]) + adv[j];
         } else {
-          const Real wJ = AFFINE ? Je * m.w[j] * wl : sgeo[(L * n + j) * GEO + DIM * DIM];
+          const Real wJ = AFFINE ? Jwl * m.w[j] : sgeo[(L * n + j) * GEO + DIM * DIM];
           res[j] = wJ * adv[j];
         }
       }
     }
     __syncthreads();
-    if (active) store_line<Real, n>(sf + a * PS + TI::line(i1, i2), TI::sw(i1), res);
+    if (active) store_line<Real, n>(sf + a * PS + own, own_swz, res);
   }
   __syncthreads();
-  // ---- outputs in node order, coalesced: element-interior nodes finish (+ A f^0, + B dt F*),
+  // ---- outputs, one thread per node and all populations in flight (coalesced across
+  //      the warp for each population): element-interior nodes finish (+ A f^0, + B dt F*),
   //      element-boundary nodes write their share to the trace T[a][e*Nb + b]
   {
     const Real *__restrict__ f0 = p.f0;
@@ -455,23 +470,34 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
     Real *__restrict__ fout = p.fout;
     Real *__restrict__ Tr = p.T;
     const size_t EN = (size_t)p.E * p.Nb;
-#pragma unroll 4
-    for (int idx = tid; idx < Q * NINT; idx += T) {
-      const int a = idx / NINT, k = idx - a * NINT;
-      const int i0 = k % (n - 2) + 1;
-      const int i1 = DIM == 3 ? (k / (n - 2)) % (n - 2) + 1 : k / (n - 2) + 1;
-      const int i2 = DIM == 3 ? k / ((n - 2) * (n - 2)) + 1 : 0;
-      const size_t gid = l2g[i0 + n * i1 + n * n * i2];
-      Real out = sf[a * PS + TI::at(i0, i1, i2)];
-      if (p.stage != 1) out += p.A * f0[(size_t)a * G + gid];
-      if (p.has_force) out += sfc[a] * rho[gid];
-      fout[(size_t)a * G + gid] = out;
-    }
-    const int Nb = p.Nb;
-#pragma unroll 4
-    for (int idx = tid; idx < Q * Nb; idx += T) {
-      const int a = idx / Nb, b = idx - a * Nb;
-      Tr[a * EN + (size_t)e * Nb + b] = sf[a * PS + TI::node(p.binv[b])];
+    for (int i = tid; i < Np; i += T) {
+      const int ti = TI::node(i);
+      const int b = p.bslot[i];
+      if (b < 0) {
+        const size_t gid = l2g[i];
+        const Real rg = p.has_force ? rho[gid] : Real(0);
+        const Real *f0p = f0 + gid;
+        Real *fo = fout + gid;
+        if (p.stage != 1) {
+#pragma unroll
+          for (int a = 0; a < Q; ++a) {
+            Real out = sf[a * PS + ti] + p.A * f0p[(size_t)a * G];
+            if (p.has_force) out += sfc[a] * rg;
+            fo[(size_t)a * G] = out;
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < Q; ++a) {
+            Real out = sf[a * PS + ti];
+            if (p.has_force) out += sfc[a] * rg;
+            fo[(size_t)a * G] = out;
+          }
+        }
+      } else {
+        Real *tp = Tr + (size_t)e * p.Nb + b;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) tp[a * EN] = sf[a * PS + ti];
+      }
     }
   }
   if (nw > 0) {

@@ -485,6 +485,89 @@ __global__ void diag_partial_kernel(const Real *buf, const double *mass, int G, 
     for (int c = 0; c < 6; ++c) partial[blockIdx.x * 6 + c] = red[c][0];
 }
 
+// viscous dissipation integral of the velocity u [E][Np][dim] (local nodes):
+// eps = 2 mu sum_i (d_i u_i)^2 - (2/3) mu (div u)^2 + mu sum_{i<j} (d_i u_j + d_j u_i)^2,
+// gradients by D_hat along each reference axis and the chain rule; one CTA per element,
+// per-element sums into partial[e] (summed in element order afterwards)
+template <typename Real>
+__global__ void eps_kernel(const double *u, int dim, int n, int Np, int affine, const Real *el_drdx, const Real *drdx,
+                           const Real *el_J, const Real *wJ, const Real *gllw, const Real *Dm, double mu,
+                           double *partial) {
+  __shared__ double red[256];
+  const int e = blockIdx.x, tid = threadIdx.x;
+  double acc = 0.0;
+  for (int i = tid; i < Np; i += blockDim.x) {
+    const int ii[3] = {i % n, (i / n) % n, dim == 3 ? i / (n * n) : 0};
+    const int st[3] = {1, n, n * n};
+    double dr[3][3];   // dr[l][c] = d u_c / d r_l
+    for (int l = 0; l < dim; ++l)
+      for (int c = 0; c < dim; ++c) {
+        double s = 0.0;
+        const int base = i - ii[l] * st[l];
+        for (int k = 0; k < n; ++k) s += (double)Dm[ii[l] * n + k] * u[((size_t)e * Np + base + k * st[l]) * dim + c];
+        dr[l][c] = s;
+      }
+    double g[3][3];    // g[k][c] = d u_c / d x_k = sum_l dr_l/dx_k d u_c/d r_l
+    for (int k = 0; k < dim; ++k)
+      for (int c = 0; c < dim; ++c) {
+        double s = 0.0;
+        for (int l = 0; l < dim; ++l) {
+          const double m = affine ? (double)el_drdx[((size_t)e * dim + l) * dim + k]
+                                  : (double)drdx[(((size_t)e * Np + i) * dim + l) * dim + k];
+          s += m * dr[l][c];
+        }
+        g[k][c] = s;
+      }
+    double div = 0.0, diag = 0.0, off = 0.0;
+    for (int k = 0; k < dim; ++k) { div += g[k][k]; diag += g[k][k] * g[k][k]; }
+    for (int a = 0; a < dim; ++a)
+      for (int b = a + 1; b < dim; ++b) off += (g[a][b] + g[b][a]) * (g[a][b] + g[b][a]);
+    const double dens = 2.0 * mu * diag - (2.0 / 3.0) * mu * div * div + mu * off;
+    double w;
+    if (affine) {
+      w = (double)el_J[e] * (double)gllw[ii[0]] * (double)gllw[ii[1]] * (dim == 3 ? (double)gllw[ii[2]] : 1.0);
+    } else {
+      w = (double)wJ[(size_t)e * Np + i];
+    }
+    acc += w * dens;
+  }
+  red[tid] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (tid < s) red[tid] += red[tid + s];
+    __syncthreads();
+  }
+  if (tid == 0) partial[e] = red[0];
+}
+
+__global__ void sum_kernel(const double *partial, int count, double *out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < count; k += blockDim.x) acc += partial[k];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+template <typename Real>
+cudaError_t launch_eps(const double *u, int dim, int n, int Np, int E, int affine, const Real *el_drdx, const Real *drdx,
+                       const Real *el_J, const Real *wJ, const Real *gllw, const Real *Dm, double mu, double *partial,
+                       double *out, cudaStream_t s) {
+  eps_kernel<Real><<<E, 256, 0, s>>>(u, dim, n, Np, affine, el_drdx, drdx, el_J, wJ, gllw, Dm, mu, partial);
+  sum_kernel<<<1, 256, 0, s>>>(partial, E, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_eps<double>(const double *, int, int, int, int, int, const double *, const double *,
+                                        const double *, const double *, const double *, const double *, double,
+                                        double *, double *, cudaStream_t);
+template cudaError_t launch_eps<float>(const double *, int, int, int, int, int, const float *, const float *,
+                                       const float *, const float *, const float *, const float *, double, double *,
+                                       double *, cudaStream_t);
+
 __global__ void diag_final_kernel(const double *partial, int nblocks, double *out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double acc[6] = {0, 0, 0, 0, 0, 0};

@@ -26,7 +26,6 @@ struct KParams {
   const int32_t *l2g;        // [E][Np]
   const uint8_t *owner;      // [E][Np]
   const int32_t *bslot;      // [Np] boundary slot of each local node, -1 inside
-  const int32_t *binv;       // [Nb] local node of each boundary slot
   const Real *el_drdx;       // [E][dim][dim] affine metrics
   const Real *el_J;          // [E]
   const Real *drdx;          // [E][Np][dim][dim] general metrics
@@ -79,6 +78,11 @@ template <typename Real>
 bool launch_fast_d3q19(int N, bool affine, const KParams<Real> &p, const FastHost &f, cudaStream_t s, cudaError_t *err);
 template <typename Real>
 bool launch_fast_d3q27(int N, bool affine, const KParams<Real> &p, const FastHost &f, cudaStream_t s, cudaError_t *err);
+
+template <typename Real>
+cudaError_t launch_eps(const double *u, int dim, int n, int Np, int E, int affine, const Real *el_drdx, const Real *drdx,
+                       const Real *el_J, const Real *wJ, const Real *gllw, const Real *Dm, double mu, double *partial,
+                       double *out, cudaStream_t s);
 
 void upload_lattice_constants();
 size_t stage_smem_bytes(int lat, int Np, int n, int real_size);

@@ -5,11 +5,14 @@ against the order N+4 run, network training and inference); this module only
 schedules the runs and moves tensors.
 
 Data: runs of the same case at the fixed filter strengths of a sweep
-(default gamma in {0.01, 0.03, 0.1, 0.3} at kc = N-2) and one run at order N+4
-with a time step dividing the order-N step.  At each snapshot every element
-gets the features of the default-filter run (the one the control replaces) and
-the label (gamma*, kc*) of the sweep setting whose element error against the
-N+4 run is smallest.
+(default gamma in {0.01, 0.03, 0.1, 0.3} at kc = N-2, optionally kc in
+{N-3, N-2, N-1}) and one run at order N+4 with a time step dividing the
+order-N step.  At each snapshot every element gets the features of the
+default-filter run (the one the control replaces) and the label (gamma*, kc*)
+of the sweep setting whose element error against the N+4 run is smallest;
+when the default setting's error is within `tie_margin` of the smallest, the
+label is the default (in well-resolved regions the settings differ by less
+than the noise of the reference and the control should keep the fixed filter).
 
 python -m paper_2509_19171_gb300.learn --case tgv3d --out weights/...npz
 """
@@ -48,7 +51,7 @@ def _handles(mesh, lattice, N, nu, sweep, default, precision, dt, ref_sub, init)
 
 
 def generate(mesh, lattice, N, nu, inits, snapshots, interval, start=0, gammas=DEFAULT_GAMMAS, kcs=None,
-             default_gamma=0.1, precision=FP32DEV, cfl=0.5, verbose=False):
+             default_gamma=0.1, precision=FP32DEV, cfl=0.5, tie_margin=0.0, verbose=False):
     """Returns X [M, 2(N+1)] raw features (float32) and Y [M, 2] labels (gamma*, kc*)."""
     import torch
     kcs = kcs or (float(N - 2),)
@@ -78,6 +81,9 @@ def generate(mesh, lattice, N, nu, inits, snapshots, interval, start=0, gammas=D
             feat = runs[base_i].features()
             errs = torch.stack([h.element_errors(ref) for h in runs])         # [runs, E]
             best = torch.argmin(errs, dim=0)
+            if tie_margin > 0:
+                emin = errs.min(dim=0).values
+                best = torch.where(errs[base_i] <= (1.0 + tie_margin) * emin, torch.full_like(best, base_i), best)
             X.append(feat.clone())
             Y.append(labels[best])
         for h in runs + [ref]:
@@ -163,25 +169,58 @@ def main():
     ap.add_argument("--interval", type=int, default=100)
     ap.add_argument("--start", type=int, default=400)
     ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--all-kc", action="store_true", help="sweep kc in {N-3, N-2, N-1} as well as gamma")
+    ap.add_argument("--eval-steps", type=int, default=0, help="held-out evaluation length (0: data horizon)")
+    ap.add_argument("--tie-margin", type=float, default=0.0)
+    ap.add_argument("--extra-n", type=int, default=0, help="also take data from a cube of this size")
+    ap.add_argument("--extra-start", type=int, default=1600)
+    ap.add_argument("--extra-interval", type=int, default=200)
+    ap.add_argument("--extra-seeds", type=int, default=3)
     ap.add_argument("--out", default=os.path.join(WEIGHTS_DIR, "learned_filter_tgv3d_n7_d3q27.npz"))
+    ap.add_argument("--check-n", type=int, default=16, help="cube size at which to report the fallback rate")
+    ap.add_argument("--check-steps", type=int, default=400)
     args = ap.parse_args()
     import workloads as W
     case = W.tgv3d_case(n=args.n)
     N = case.order
     t0 = time.time()
+    kcs = (float(N - 3), float(N - 2), float(N - 1)) if args.all_kc else None
     X, Y = generate(case.mesh, case.lattice, N, case.nu, tgv_inits(args.seeds), args.snapshots, args.interval,
-                    start=args.start, verbose=True)
+                    start=args.start, kcs=kcs, tie_margin=args.tie_margin, verbose=True)
+    extra_eval = None
+    if args.extra_n:
+        import torch
+        ec = W.tgv3d_case(n=args.extra_n)
+        X2, Y2 = generate(ec.mesh, ec.lattice, N, ec.nu, tgv_inits(args.extra_seeds, seed0=7), args.snapshots,
+                          args.extra_interval, start=args.extra_start, kcs=kcs, tie_margin=args.tie_margin, verbose=True)
+        X, Y = torch.cat([X, X2]), torch.cat([Y, Y2])
+        extra_eval = ec
     t1 = time.time()
     params, lo, hi, hist = train(X, Y, N, epochs=args.epochs, verbose=True)
     t2 = time.time()
     res, fb = evaluate(case.mesh, case.lattice, N, case.nu, tgv_inits(1, seed0=99)[0],
-                       args.start + args.snapshots * args.interval, params, lo, hi)
+                       args.eval_steps or (args.start + args.snapshots * args.interval), params, lo, hi)
+    res_extra = None
+    if extra_eval is not None:
+        res_extra = evaluate(extra_eval.mesh, extra_eval.lattice, N, extra_eval.nu, tgv_inits(1, seed0=99)[0],
+                             args.extra_start + args.snapshots * args.extra_interval, params, lo, hi)
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     np.savez(args.out, params=params, lo=lo, hi=hi, N=N, lattice=case.lattice, samples=int(X.shape[0]),
              loss=np.array(hist, np.float32))
+    big = W.tgv3d_case(n=args.check_n)
+    h = SELBM(big.mesh, big.lattice, N, big.nu, cfl=big.cfl, precision=FP32DEV, filt=big.filt)
+    h.init_from(big.init)
+    h.set_learned_filter(params, lo, hi)
+    h.step(args.check_steps)
+    st = h.learned_status()
+    h.close()
     print({"samples": int(X.shape[0]), "data_s": round(t1 - t0, 1), "train_s": round(t2 - t1, 1),
-           "label_hist": np.unique(Y[:, 0].cpu().numpy(), return_counts=True)[1].tolist(),
-           "eval": res, "fallback_element_steps": fb})
+           "label_hist": {f"{g:.2f}/{k:.0f}": int(c) for (g, k), c in
+                          zip(*np.unique(Y.cpu().numpy().round(3), axis=0, return_counts=True))},
+           "eval": res, "fallback_element_steps": fb, "eval_extra": res_extra,
+           "check": {"n": args.check_n, "steps": args.check_steps,
+                     "fallback_fraction": st["fixed_element_steps"] / (big.mesh.nelem * (args.check_steps - 1)),
+                     "flag": st["fallback_flag"]}})
 
 
 if __name__ == "__main__":

@@ -102,6 +102,8 @@ def test_shear_layer_100_steps(P):
     d = s.diagnostics()
     m, mom, ke = o.integrals(f)
     assert abs(d[0] - m) <= 1e-12 * m and abs(d[4] - ke) <= 1e-9 * ke
+    eps = o.dissipation(f)
+    assert abs(d[5] - eps) <= 1e-9 * abs(eps)
 
 
 @pytest.mark.parametrize("lat,N", [("D3Q19", 5), ("D3Q27", 5), ("D3Q27", 7), ("D3Q19", 7)])
@@ -119,6 +121,8 @@ def test_tgv3d_box_quadratic_filter(P, lat, N):
     f = o.run(f, 9)
     s.step(9)
     assert rel(s.get_state(), o.to_local(f)) <= 1e-11
+    d = s.diagnostics()
+    assert abs(d[5] - o.dissipation(f)) <= 1e-9 * abs(o.dissipation(f))
 
 
 @pytest.mark.parametrize("N,prec", [(4, 0), (7, 0), (7, 1)])
@@ -186,6 +190,20 @@ def test_generic_kernel_matches_oracle(P, monkeypatch):
     f = random_continuous_state(o, 0.03, 8)
     f = check_one_step(P, o, s, f, 1e-12)
     check_one_step(P, o, s, f, 1e-12)
+
+
+def test_graph_launch_matches_eager(P, monkeypatch):
+    """Captured steps (CUDA graphs) give bit-identical states to eager launches."""
+    mesh = W.box_mesh((3, 2), (0, 0), (1, 1), (True, False), walls={2: 1, 3: 2}, wall_velocity=[[0, 0], [0.01, 0]])
+    filt = {"shape": 0, "gamma": 0.1, "kc": 6.0}
+    init = W.shear_layer_init(U0=0.02, kappa=5.0)
+    a = P.SELBM(mesh, "D2Q9", 8, 1e-3, filt=filt)
+    monkeypatch.setenv("SELBM_NO_GRAPH", "1")
+    b = P.SELBM(mesh, "D2Q9", 8, 1e-3, filt=filt)
+    for h in (a, b):
+        h.init_from(init)
+        h.step(25)
+    assert np.array_equal(a.get_state(), b.get_state())
 
 
 def test_fp32_deviation_form(P):
