@@ -78,15 +78,32 @@ def counts(case, info):
     return dict(E=E, Np=Np, Nb=Nb, G=info["G"], Gb=info["Gb"], Gint=Gint, ENb=E * Nb)
 
 
-def bytes_per_step(c, Q, rsz, affine):
-    """Algorithmic DRAM bytes of one step: (stage1, stage2+3 per launch, assembly s1, assembly s2/3)."""
-    G, Gint, ENb, Gb = c["G"], c["Gint"], c["ENb"], c["Gb"]
-    geo = 0 if affine else (c["E"] * c["Np"] * 10 * rsz)     # per-node metrics + wJ read by each stage
-    s1 = (G + G + Gint + ENb) * Q * rsz + geo
-    s23 = (G + Gint + Gint + ENb) * Q * rsz + geo
-    a1 = (ENb + 2 * Gb) * Q * rsz
-    a23 = (ENb + 3 * Gb) * Q * rsz
-    return s1, s23, a1, a23
+def kernel_bytes(c, Q, rsz, affine, split, learned):
+    """Algorithmic DRAM bytes per launch of each kernel kind on the unique-node layout:
+    every unique value read once and written once per pass, shares of element-boundary
+    nodes (E*Nb per population) written and read once, per-node metrics on curved meshes."""
+    G, Gint, ENb, Gb, E, Np = c["G"], c["Gint"], c["ENb"], c["Gb"], c["E"], c["Np"]
+    geo = 0 if affine else E * Np * 10 * rsz          # per-node metrics + wJ read by each stage
+    kb = {"stage23": (G + Gint + Gint + ENb) * Q * rsz + geo,          # f^{s-1}, f^0 (interior), f^s, trace
+          "assembly": ((ENb + 2 * Gb) + 2 * (ENb + 3 * Gb)) * Q * rsz / 3}
+    if split:
+        kb["stage1"] = (G + Gint + ENb) * Q * rsz + geo                # f^0 -> f^1 (interior), trace
+        kb["prologue"] = 2 * G * Q * rsz                               # f -> (filter, collision) -> f^0
+        # learned: f -> features, network, per-element filter; interior f^0 + boundary shares;
+        # then the shares' assembly + collision on shared nodes
+        kb["learned"] = (G + Gint + ENb) * Q * rsz + (ENb + Gb) * Q * rsz + (0 if affine else E * Np * rsz)
+    else:
+        kb["stage1"] = (G + G + Gint + ENb) * Q * rsz + geo            # f, f^0 out, f^1 (interior), trace
+        kb["learned"] = (G + Gint + ENb) * Q * rsz + (ENb + Gb) * Q * rsz + (0 if affine else E * Np * rsz)
+    return kb
+
+
+def launches_per_step(split, learned):
+    """Kernels one step launches: 3 x (stage + assembly), plus the collision/filter
+    prologue of the split form, plus control + drift check + share assembly when learned."""
+    if split:
+        return 6 + (3 if learned else 1)
+    return 6 + (3 if learned else 0)
 
 
 def flops_per_step(case, e_nonzero_axes, Q):
@@ -348,30 +365,30 @@ def main():
         Q = s.Q
         upd_step = case.mesh.nelem * info["Np"] * Q
         value = job_throughput(upd_step, args.steps, world, ms)
-        s1, s23, a1, a23 = bytes_per_step(c, Q, rsz, info["affine"])
-        f1, f23 = flops_per_step(case, nz_axes, Q)
-        st1_ms = t["stage1"][0] / max(t["stage1"][1], 1)
-        st23_ms = t["stage23"][0] / max(t["stage23"][1], 1)
-        as_ms = t["assembly"][0] / max(t["assembly"][1], 1)
-        lc_ms = t["other"][0] / max(t["other"][1], 1)
-        stage_ms = (t["stage1"][0] + t["stage23"][0]) / max(t["stage1"][1] + t["stage23"][1], 1)
-        stage_bytes = (s1 + 2 * s23) / 3
-        stage_flops = (f1 + 2 * f23) / 3
-        step_bytes = s1 + 2 * s23 + a1 + 2 * a23
         learned = form == "fp32dev_learned"
+        kb = kernel_bytes(c, Q, rsz, info["affine"], s.split, learned)
+        f1, f23 = flops_per_step(case, nz_axes, Q)
+        per = {k: t[k][0] / t[k][1] for k in t if t[k][1] > 0}          # ms per launch (group)
+        kernel_ms = {k: per[k] for k in per}
+        kernel_frac = {k: kb[k] / (per[k] * 1e-3) / 1e9 / hbm for k in per if k in kb}
+        step_bytes = kb["stage1"] + 2 * kb["stage23"] + 3 * kb["assembly"]
+        step_bytes += kb["learned"] if learned else (kb["prologue"] if s.split else 0)
         entry = {
             "value": value, "ms_per_step": ms / args.steps, "dtype": "f64" if form == "fp64" else "f32",
-            "kernel_ms": {"stage1": st1_ms, "stage2_3": st23_ms, "assembly": as_ms},
-            "launches_per_step": 6 + (3 if learned else 0),
+            "step_form": "population-split" if s.split else "whole-element",
+            "kernel_ms": kernel_ms, "kernel_hbm_frac_alg": kernel_frac,
+            "launches_per_step": launches_per_step(s.split, learned),
             "hbm_gbs_alg_step": step_bytes / (ms / args.steps * 1e-3) / 1e9,
-            "stage_hbm_frac": stage_bytes / (stage_ms * 1e-3) / 1e9 / hbm,
-            "stage_fp64_frac": (stage_flops / (stage_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS) if form == "fp64" else None,
-            "stage_bytes": stage_bytes, "stage_flops": stage_flops, "stage_ms": stage_ms,
             "bytes_per_update": step_bytes / upd_step,
+            "stage23_bytes": kb["stage23"], "stage23_ms": per.get("stage23"),
         }
+        if form == "fp64":
+            st_ms = (t["stage1"][0] + t["stage23"][0]) / max(t["stage1"][1] + t["stage23"][1], 1)
+            entry["stage_flops"] = (f1 + 2 * f23) / 3
+            entry["stage_ms"] = st_ms
+            entry["stage_fp64_frac"] = entry["stage_flops"] / (st_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
         if learned:
             st = s.learned_status()
-            entry["kernel_ms"]["learned_control"] = lc_ms
             entry["learned"] = {"fallback_flag": st["fallback_flag"],
                                 "fixed_element_steps": st["fixed_element_steps"],
                                 "weights": os.path.relpath(WEIGHTS, ROOT)}
@@ -400,12 +417,15 @@ def main():
         roof = {"bound": "alu", "kernel": "stage_fast_kernel (FP64 pipe)", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe: 2.07/clk/SM)",
-                "traffic": None, "hbm_frac_alg": r["stage_hbm_frac"]}
-    else:
-        achieved = r["stage_bytes"] / (r["stage_ms"] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": "stage_fast_kernel<float, D3Q27, N=7>", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "peak_source": f"{pk_kind} hbm_gbs (of {pk_kind})",
                 "traffic": None}
+    else:
+        # dominant kernel: the stage 2/3 kernel (two launches per step)
+        name = ("stage_split_kernel<float, D3Q27, N=7> (stages 2, 3)" if r["step_form"] == "population-split"
+                else "stage_fast_kernel<float, D3Q27, N=7> (stages 2, 3)")
+        achieved = r["stage23_bytes"] / (r["stage23_ms"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "peak_source": f"{pk_kind} hbm_gbs (of {pk_kind})",
+                "bytes_per_launch": r["stage23_bytes"], "traffic": None}
 
     line = {"metric": metric, "value": r["value"], "unit": "node-pop updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],

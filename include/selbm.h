@@ -114,10 +114,12 @@ void selbm_destroy(selbm_t *h);
 const char *selbm_last_error(const selbm_t *h);
 
 /*
- * Sizes and scalars: out_i[0..7] = E, Np, Q, G (unique nodes), dim, N,
- * precision, steps taken; out_d[0..3] = dt, tau, lambda, time.
+ * Sizes and scalars: out_i[0..8] = E, Np, Q, G (unique nodes), dim, N,
+ * precision, steps taken, step form (0: whole-element stage kernels, 1:
+ * population-split stages after a per-element prologue); out_d[0..3] = dt,
+ * tau, lambda, time.
  */
-int selbm_info(const selbm_t *h, int64_t out_i[8], double out_d[4]);
+int selbm_info(const selbm_t *h, int64_t out_i[9], double out_d[4]);
 /* Lattice table: e[Q][3] (zero-padded in 2D), t[Q], opposite[Q]. */
 int selbm_lattice_table(const selbm_t *h, int32_t *e, double *t, int32_t *opp);
 /* Physical coordinates of every local node, host buffer [E][Np][dim]. */
@@ -234,13 +236,21 @@ int selbm_mesh_check(const selbm_mesh *mesh, int32_t lattice, int32_t order, int
  * stream; selbm_timers(h, 0) stops.  selbm_timers_read synchronises the
  * stream and returns, per kernel kind k, the summed device time ms[k] and the
  * launch count n[k] since the last reset:
- *   k = 0: stage kernel, stage 1 (filter + collision + streaming RHS)
+ *   k = 0: stage kernel, stage 1 (whole-element form: filter + collision +
+ *          streaming RHS; population-split form: streaming RHS only)
  *   k = 1: stage kernel, stages 2 and 3
  *   k = 2: assembly kernel (all stages)
- *   k = 3: learned filter control (features, network, drift check)
+ *   k = 3: learned filter control (features, network, filter, drift check; in
+ *          the population-split form also the collision and the assembly of
+ *          the filtered copies of shared nodes)
+ *   k = 4: population-split form: prologue (fixed filter + collision, or the
+ *          collision alone when no filter is pending)
+ * The population-split form is the default for FP32 hexahedral meshes at the
+ * compiled orders (D3Q19: N = 4, 7; D3Q27: N = 5, 7).
  */
+#define SELBM_TIMER_KINDS 5
 int selbm_timers(selbm_t *h, int enable);
-int selbm_timers_read(selbm_t *h, double ms[4], int64_t n[4]);
+int selbm_timers_read(selbm_t *h, double ms[SELBM_TIMER_KINDS], int64_t n[SELBM_TIMER_KINDS]);
 
 /*
  * Allocation-free integrals of a caller-owned state.  The paper has no

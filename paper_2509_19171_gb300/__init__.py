@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(HERE, "libselbm.so")
 D2Q9, D3Q19, D3Q27 = 0, 1, 2
 LATTICES = {"D2Q9": D2Q9, "D3Q19": D3Q19, "D3Q27": D3Q27}
 FP64, FP32DEV = 0, 1
+TIMER_KINDS = 5
+TIMER_NAMES = ["stage1", "stage23", "assembly", "learned", "prologue"]
 ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_MESH", -3: "ERR_CUDA", -4: "ERR_NONFINITE", -5: "ERR_TIMEOUT", -6: "ERR_STATE"}
 
 # functions declared in include/selbm.h (checked by the ABI test)
@@ -188,10 +190,11 @@ class SELBM:
         return rc
 
     def _info(self):
-        ii = (C.c_int64 * 8)()
+        ii = (C.c_int64 * 9)()
         dd = (C.c_double * 4)()
         self._check(self.lib.selbm_info(self.h, ii, dd))
-        self.E, self.Np, self.Q, self.G, _, self.N, self.precision, self.steps = [int(x) for x in ii]
+        self.E, self.Np, self.Q, self.G, _, self.N, self.precision, self.steps, split = [int(x) for x in ii]
+        self.split = bool(split)
         self.dt, self.tau, self.lam, self.time = [float(x) for x in dd]
         return self
 
@@ -274,11 +277,11 @@ class SELBM:
         self._check(self.lib.selbm_timers(self.h, int(enable)))
 
     def timers_read(self):
-        """{kind: (ms, launches)} for kinds stage1, stage23, assembly, other."""
-        ms = np.zeros(4)
-        n = np.zeros(4, np.int64)
+        """{kind: (ms, launches)} for kinds stage1, stage23, assembly, learned, prologue."""
+        ms = np.zeros(TIMER_KINDS)
+        n = np.zeros(TIMER_KINDS, np.int64)
         self._check(self.lib.selbm_timers_read(self.h, _dptr(ms), n.ctypes.data_as(C.POINTER(C.c_int64))))
-        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(["stage1", "stage23", "assembly", "other"])}
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(TIMER_NAMES)}
 
     def sync(self):
         self._check(self.lib.selbm_sync(self.h))

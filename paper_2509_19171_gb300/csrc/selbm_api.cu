@@ -45,6 +45,10 @@ struct selbm {
   int64_t steps = 0;
   bool initialized = false, filter_pending = false, filter_on = false, has_force = false;
   bool use_fast = true;   // SELBM_GENERIC_KERNEL=1 in the environment selects the generic stage kernel
+  // population-split step (prologue + split stages); default for FP32 hexahedral meshes,
+  // SELBM_SPLIT=1 / 0 in the environment forces it on / off where it is compiled
+  bool use_split = false;
+  std::vector<double> Vm_h, Vinv_h;   // modal <-> nodal matrices
   // learned per-element filter control
   bool learned = false;
   int nin = 0;
@@ -152,6 +156,8 @@ cudaError_t upload_real(selbm *h) {
   {
     std::vector<double> V, Vi;
     build_modal(S.gll, &V, &Vi);
+    h->Vm_h = V;
+    h->Vinv_h = Vi;
     if ((e = upload(&p, cast_vec<Real>(V)))) return e; h->d_Vm = p; h->allocs.push_back(p);
     if ((e = upload(&p, cast_vec<Real>(Vi)))) return e; h->d_Vinv = p; h->allocs.push_back(p);
   }
@@ -263,10 +269,90 @@ cudaError_t launch_stage_any(selbm *h, const KParams<Real> &p) {
   return launch_stage<Real>(h->lat, h->S.affine, p, h->stream);
 }
 
+SplitHost split_host(selbm *h) {
+  return SplitHost{h->S.gll.D.data(), h->FU.data(), h->FW.data(), h->S.gll.w.data(), h->Fr,
+                   h->Vm_h.data(), h->Vinv_h.data(), h->sigma.data()};
+}
+
+template <typename Real>
+cudaError_t launch_split_stage(selbm *h, const KParams<Real> &p) {
+  const SplitHost sh = split_host(h);
+  cudaError_t err = cudaErrorInvalidValue;
+  if (h->lat == SELBM_D3Q19) split_stage_d3q19<Real>(h->S.N, h->S.affine, p, sh, h->stream, &err);
+  else if (h->lat == SELBM_D3Q27) split_stage_d3q27<Real>(h->S.N, h->S.affine, p, sh, h->stream, &err);
+  return err;
+}
+
+template <typename Real>
+cudaError_t launch_split_prologue(selbm *h, int mode, const KParams<Real> &p, const LearnedPtrs<Real> &lp) {
+  const SplitHost sh = split_host(h);
+  cudaError_t err = cudaErrorInvalidValue;
+  if (h->lat == SELBM_D3Q19) split_prologue_d3q19<Real>(h->S.N, h->S.affine, mode, p, sh, lp, h->stream, &err);
+  else if (h->lat == SELBM_D3Q27) split_prologue_d3q27<Real>(h->S.N, h->S.affine, mode, p, sh, lp, h->stream, &err);
+  return err;
+}
+
+template <typename Real>
+cudaError_t launch_split_collide(selbm *h, int which, const KParams<Real> &p) {
+  if (h->lat == SELBM_D3Q19) return split_collide_d3q19<Real>(which, p, h->stream);
+  if (h->lat == SELBM_D3Q27) return split_collide_d3q27<Real>(which, p, h->stream);
+  return cudaErrorInvalidValue;
+}
+
+template <typename Real>
+LearnedPtrs<Real> learned_ptrs(selbm *h, bool with_drift) {
+  LearnedPtrs<Real> lp{};
+  lp.W = h->d_W; lp.lo = (const Real *)h->d_lo; lp.hi = (const Real *)h->d_hi;
+  lp.flag = h->d_flag; lp.acc = with_drift ? h->d_acc : nullptr;
+  lp.sigma_out = (Real *)h->d_sigma_e; lp.feat_out = nullptr; lp.n_fallback = with_drift ? h->d_nfb : nullptr;
+  lp.outputs = 1;
+  return lp;
+}
+
+// one time step of the population-split form: prologue (pending filter + collision,
+// f^0 on unique nodes), then three advection stages, each = split kernel + assembly
+template <typename Real>
+cudaError_t enqueue_step_split(selbm *h, bool apply_filter) {
+  KParams<Real> p = base_params<Real>(h);
+  Real *FA = (Real *)h->FA, *F0 = (Real *)h->F0, *F2 = (Real *)h->F2;
+  cudaError_t e;
+  p.fin = FA; p.f0out = F0;
+  p.stage = 1; p.A = Real(0); p.B = Real(1);
+  if (apply_filter && h->learned) {
+    cudaEvent_t t0 = h->mark_begin();
+    if ((e = launch_split_prologue<Real>(h, PRO_LEARNED, p, learned_ptrs<Real>(h, true)))) return e;
+    if ((e = launch_drift_check(h->d_acc, h->d_flag, h->mass_bound, h->ke_bound, h->has_force ? 0 : 1, h->stream))) return e;
+    if ((e = launch_split_collide<Real>(h, 1, p))) return e;
+    h->mark_end(3, t0);
+  } else {
+    cudaEvent_t t0 = h->mark_begin();
+    if (apply_filter) e = launch_split_prologue<Real>(h, PRO_FIXED, p, LearnedPtrs<Real>{});
+    else e = launch_split_collide<Real>(h, 0, p);
+    if (e) return e;
+    h->mark_end(4, t0);
+  }
+  const Real A[3] = {Real(0), Real(0.75), Real(1.0 / 3.0)};
+  const Real B[3] = {Real(1), Real(0.25), Real(2.0 / 3.0)};
+  const Real *fin[3] = {F0, FA, F2};   // f^{s-1}: stage 1 advects f^0
+  Real *fout[3] = {FA, F2, FA};
+  for (int s = 0; s < 3; ++s) {
+    p.stage = s + 1; p.A = A[s]; p.B = B[s]; p.apply_filter = 0;
+    p.fin = fin[s]; p.f0 = F0; p.fout = fout[s]; p.f0out = nullptr;
+    cudaEvent_t t0 = h->mark_begin();
+    if ((e = launch_split_stage<Real>(h, p))) return e;
+    h->mark_end(s == 0 ? 0 : 1, t0);
+    t0 = h->mark_begin();
+    if ((e = launch_dss<Real>(h->lat, p, h->stream))) return e;
+    h->mark_end(2, t0);
+  }
+  return cudaSuccess;
+}
+
 // one time step: three stages, each = element kernel + assembly kernel
 template <typename Real>
 cudaError_t enqueue_step(selbm *h, bool apply_filter) {
   KParams<Real> p = base_params<Real>(h);
+  if (h->use_split) return enqueue_step_split<Real>(h, apply_filter);
   Real *FA = (Real *)h->FA, *F0 = (Real *)h->F0, *F2 = (Real *)h->F2;
   const Real A[3] = {Real(0), Real(0.75), Real(1.0 / 3.0)};
   const Real B[3] = {Real(1), Real(0.25), Real(2.0 / 3.0)};
@@ -371,6 +457,11 @@ int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_
   if (rc != SELBM_OK) { g_create_error = err; delete h; return rc; }
   Setup &S = h->S;
   h->Q = S.lat.Q;
+  {
+    const char *sp = std::getenv("SELBM_SPLIT");
+    const bool ok = h->use_fast && S.dim == 3 && split_compiled(h->lat, S.N);
+    h->use_split = ok && (sp && sp[0] ? sp[0] == '1' : h->prec == SELBM_FP32DEV);
+  }
   const size_t smem = stage_smem_bytes(h->lat, S.Np, S.n1, h->rsz);
   if (smem > 227 * 1024) { g_create_error = "element tile does not fit in shared memory (use FP32 or a lower order)"; delete h; return SELBM_ERR_ARG; }
   h->dt = params->dt > 0.0 ? params->dt : params->cfl * S.min_spacing;
@@ -418,11 +509,12 @@ void selbm_destroy(selbm_t *h) {
 
 const char *selbm_last_error(const selbm_t *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
-int selbm_info(const selbm_t *h, int64_t out_i[8], double out_d[4]) {
+int selbm_info(const selbm_t *h, int64_t out_i[9], double out_d[4]) {
   if (!h) return SELBM_ERR_ARG;
   if (out_i) {
     out_i[0] = h->S.E; out_i[1] = h->S.Np; out_i[2] = h->Q; out_i[3] = h->S.G;
     out_i[4] = h->S.dim; out_i[5] = h->S.N; out_i[6] = h->prec; out_i[7] = h->steps;
+    out_i[8] = h->use_split ? 1 : 0;
   }
   if (out_d) { out_d[0] = h->dt; out_d[1] = h->tau; out_d[2] = h->lam; out_d[3] = h->time; }
   return SELBM_OK;
@@ -674,11 +766,11 @@ int selbm_timers(selbm_t *h, int enable) {
   return SELBM_OK;
 }
 
-int selbm_timers_read(selbm_t *h, double ms[4], int64_t n[4]) {
+int selbm_timers_read(selbm_t *h, double ms[SELBM_TIMER_KINDS], int64_t n[SELBM_TIMER_KINDS]) {
   if (!h || !ms || !n) return SELBM_ERR_ARG;
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "timers");
-  for (int k = 0; k < 4; ++k) { ms[k] = 0.0; n[k] = 0; }
+  for (int k = 0; k < SELBM_TIMER_KINDS; ++k) { ms[k] = 0.0; n[k] = 0; }
   for (auto &u : h->ev_used) {
     float t = 0.f;
     if (cudaEventElapsedTime(&t, u.second.first, u.second.second) == cudaSuccess) {

@@ -1,7 +1,10 @@
 // Device-side data structures and launch helpers of the filtered SELBM hot path.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+
+#include "../../include/selbm.h"
 
 namespace slb {
 
@@ -78,6 +81,44 @@ template <typename Real>
 bool launch_fast_d3q19(int N, bool affine, const KParams<Real> &p, const FastHost &f, cudaStream_t s, cudaError_t *err);
 template <typename Real>
 bool launch_fast_d3q27(int N, bool affine, const KParams<Real> &p, const FastHost &f, cudaStream_t s, cudaError_t *err);
+
+// population-split step (3D; orders compiled for D3Q19: 4, 7 and D3Q27: 5, 7)
+struct SplitHost {
+  const double *D, *U, *W, *w;   // D_hat; fixed filter F = I + U W; GLL weights
+  int r;
+  const double *Vm, *Vinv, *fixed_sigma;   // modal <-> nodal; transfer function of the fixed filter
+};
+template <typename Real>
+struct LearnedPtrs {
+  const __nv_bfloat16 *W;        // network parameters; NULL = features only
+  const Real *lo, *hi;           // [2n] training range of the features
+  const int *flag;               // sticky drift fallback flag or NULL
+  double *acc;                   // drift accumulators or NULL
+  Real *sigma_out;               // [E][n] or NULL
+  float *feat_out;               // [E][2n] or NULL
+  int *n_fallback;               // elements that kept the fixed filter, or NULL
+  int outputs;                   // 0: features / transfer functions only
+};
+enum { PRO_FIXED = 1, PRO_LEARNED = 2 };
+template <typename Real>
+bool split_stage_d3q19(int N, bool affine, const KParams<Real> &p, const SplitHost &h, cudaStream_t s, cudaError_t *err);
+template <typename Real>
+bool split_stage_d3q27(int N, bool affine, const KParams<Real> &p, const SplitHost &h, cudaStream_t s, cudaError_t *err);
+template <typename Real>
+bool split_prologue_d3q19(int N, bool affine, int mode, const KParams<Real> &p, const SplitHost &h,
+                          const LearnedPtrs<Real> &lp, cudaStream_t s, cudaError_t *err);
+template <typename Real>
+bool split_prologue_d3q27(int N, bool affine, int mode, const KParams<Real> &p, const SplitHost &h,
+                          const LearnedPtrs<Real> &lp, cudaStream_t s, cudaError_t *err);
+// which: 0 collision on unique nodes (writes fout -> f0out), 1 assembly of the learned
+// filter's weighted shares at shared nodes + collision
+template <typename Real>
+cudaError_t split_collide_d3q19(int which, const KParams<Real> &p, cudaStream_t s);
+template <typename Real>
+cudaError_t split_collide_d3q27(int which, const KParams<Real> &p, cudaStream_t s);
+inline bool split_compiled(int lat, int N) {
+  return (lat == SELBM_D3Q19 && (N == 4 || N == 7)) || (lat == SELBM_D3Q27 && (N == 5 || N == 7));
+}
 
 template <typename Real>
 cudaError_t launch_eps(const double *u, int dim, int n, int Np, int E, int affine, const Real *el_drdx, const Real *drdx,

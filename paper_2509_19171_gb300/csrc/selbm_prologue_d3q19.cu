@@ -1,0 +1,32 @@
+// Instantiations of the per-element prologue (pending filter + collision) for
+// D3Q19 (orders: 4 7).
+#include "selbm_split.cuh"
+
+namespace slb {
+
+template <typename Real, int n>
+static cudaError_t prologue_n(bool affine, int mode, const KParams<Real> &p, const SplitHost &h,
+                              const LearnedPtrs<Real> &lp, cudaStream_t s) {
+  if (mode == PRO_LEARNED)
+    return affine ? launch_prologue_t<Real, SELBM_D3Q19, n, true, PRO_LEARNED>(p, h, lp, s)
+                  : launch_prologue_t<Real, SELBM_D3Q19, n, false, PRO_LEARNED>(p, h, lp, s);
+  return affine ? launch_prologue_t<Real, SELBM_D3Q19, n, true, PRO_FIXED>(p, h, lp, s)
+                : launch_prologue_t<Real, SELBM_D3Q19, n, false, PRO_FIXED>(p, h, lp, s);
+}
+
+template <typename Real>
+bool split_prologue_d3q19(int N, bool affine, int mode, const KParams<Real> &p, const SplitHost &h,
+                         const LearnedPtrs<Real> &lp, cudaStream_t s, cudaError_t *err) {
+  switch (N) {
+    case 4: *err = prologue_n<Real, 5>(affine, mode, p, h, lp, s); return true;
+    case 7: *err = prologue_n<Real, 8>(affine, mode, p, h, lp, s); return true;
+  }
+  return false;
+}
+
+template bool split_prologue_d3q19<float>(int, bool, int, const KParams<float> &, const SplitHost &,
+                                         const LearnedPtrs<float> &, cudaStream_t, cudaError_t *);
+template bool split_prologue_d3q19<double>(int, bool, int, const KParams<double> &, const SplitHost &,
+                                          const LearnedPtrs<double> &, cudaStream_t, cudaError_t *);
+
+}  // namespace slb

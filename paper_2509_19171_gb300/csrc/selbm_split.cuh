@@ -1,0 +1,766 @@
+// Population-split step for hexahedral meshes (compile-time order N and lattice).
+//
+// Once the collision is done, the three Runge-Kutta stages only advect, and every
+// population advects independently of the others.  The step therefore runs as
+//   prologue_kernel   one CTA per element: the pending filter of the previous step
+//                     (fixed, or chosen per element by the learned control) and the
+//                     BGK collision; writes f^0 on unique nodes
+//   stage_split_kernel  per stage, one CTA per (element, group of PB populations):
+//                     gather the group's tile, -B dt e.grad f by sum factorisation,
+//                     stage combination, element-interior nodes to f^s and weighted
+//                     boundary shares to the assembly trace (+ flux bounce-back)
+//   dss_kernel        assembly of shared nodes (unchanged)
+// The split CTAs are small (PB (N+1)^3 values), a single round of (population,
+// r-line) tasks covers them, and several CTAs per SM overlap their gathers with
+// each other's arithmetic.
+//
+// With the learned control, copies of a shared node are filtered by different
+// element filters; the prologue writes their weighted shares wJ f to the trace and
+// dss_collide_kernel forms the mass-weighted average and collides it.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "selbm_collide.cuh"
+#include "selbm_fast.cuh"
+
+namespace slb {
+
+// asynchronous global -> shared copy of one value (cp.async, 4 or 8 bytes)
+template <typename Real>
+__device__ __forceinline__ void cp_async(Real *dst, const Real *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(Real) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <int LAT, int n>
+struct SplitShape {
+  static constexpr int Q = LT<LAT>::v.Q;
+  static constexpr int Np = n * n * n, NL = n * n;
+  static constexpr int PB = (256 / NL) < 1 ? 1 : (256 / NL);     // populations per CTA
+  static constexpr int THREADS = PB * NL;                         // one (population, r-line) task each
+  static constexpr int NG = (Q + PB - 1) / PB;                    // CTAs per element
+  static constexpr int GEO = 10;
+  static constexpr int NPT = (Np + THREADS - 1) / THREADS;        // nodes per thread when gathering
+};
+
+template <typename Real, int LAT, int n, bool AFFINE>
+constexpr size_t split_smem_bytes(int wall_max) {
+  using S = SplitShape<LAT, n>;
+  using TI = Tile<Real, n, 3>;
+  size_t reals = (size_t)S::PB * TI::PS + n * n + S::PB * 3 + S::PB + n + (size_t)S::PB * S::Np;
+  if (!AFFINE) reals += (size_t)S::Np * S::GEO;
+  reals += (size_t)S::PB * wall_max;
+  return reals * sizeof(Real);
+}
+
+// ---------------------------------------------------------------------------
+// one Runge-Kutta stage for PB populations of one element
+// ---------------------------------------------------------------------------
+template <typename Real, int LAT, int n, bool AFFINE>
+__global__ void __launch_bounds__(SplitShape<LAT, n>::THREADS, (sizeof(Real) == 4 ? 4 : 2))
+stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
+  using S = SplitShape<LAT, n>;
+  constexpr int Q = S::Q, DIM = 3, Np = S::Np, NL = S::NL, T = S::THREADS, PB = S::PB, NG = S::NG;
+  constexpr int GEO = S::GEO, NPT = S::NPT;
+  using TI = Tile<Real, n, DIM>;
+  constexpr int PS = TI::PS;
+  constexpr VelTab V = LT<LAT>::v;
+  constexpr int KU = sizeof(Real) == 4 ? n : 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real *sf = reinterpret_cast<Real *>(smem_raw);   // [PB][PS] tile of the group
+  Real *sD = sf + PB * PS;                          // [n][n]
+  Real *scoef = sD + n * n;                         // [PB][DIM] (affine: -B dt sum_k e_k dr_l/dx_k)
+  Real *sfc = scoef + PB * DIM;                     // [PB]      B dt F*_a / rho
+  Real *sw = sfc + PB;                              // [n]
+  Real *sgeo = sw + n;                              // [Np][GEO] (curved: -B dt dr_l/dx_k, wJ)
+  Real *sf0 = sgeo + (AFFINE ? 0 : Np * GEO);       // [PB][Np] f^0 of element-interior nodes
+  Real *wbuf = sf0 + PB * Np;                       // [wall nodes][PB]
+  const int e = blockIdx.x / NG, a0 = (blockIdx.x - e * NG) * PB;
+  const int na = Q - a0 < PB ? Q - a0 : PB;
+  const int tid = threadIdx.x;
+  const Real Bdt = p.B * p.dt;
+  const int32_t *l2g = p.l2g + (size_t)e * Np;
+  const size_t G = p.G;
+
+  for (int k = tid; k < n * n; k += T) sD[k] = m.D[k];
+  if (tid < n) sw[tid] = m.w[tid];
+  if (tid < na) {
+    const int a = a0 + tid;
+    static_for<0, Q>([&](auto ac) {
+      constexpr int aa = decltype(ac)::value;
+      if (aa == a) {
+        if (AFFINE) {
+#pragma unroll
+          for (int l = 0; l < DIM; ++l) {
+            Real c = 0;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k)
+              if (V.e[aa][k] != 0) c += (V.e[aa][k] > 0 ? Real(1) : Real(-1)) * p.el_drdx[((size_t)e * DIM + l) * DIM + k];
+            scoef[tid * DIM + l] = -Bdt * c;
+          }
+        }
+        Real ge = 0;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          if (V.e[aa][k] != 0) ge += (V.e[aa][k] > 0 ? Real(1) : Real(-1)) * p.g[k];
+        sfc[tid] = Bdt * Real(V.t[aa]) * Real(3) * ge;
+      }
+    });
+  }
+  // ---- gather the group's tile, and f^0 of element-interior nodes for the output,
+  //      with asynchronous copies (no register staging, all of them in flight at once)
+  {
+    const Real *fin = p.fin;
+    const Real *f0 = p.f0;
+#pragma unroll
+    for (int r = 0; r < NPT; ++r) {
+      const int i = tid + r * T;
+      if (i < Np) {
+        const int g = l2g[i];
+        const int b = p.bslot[i];
+        const int ti = TI::node(i);
+#pragma unroll
+        for (int pl = 0; pl < PB; ++pl) {
+          if (pl < na) {
+            const size_t ga = (size_t)(a0 + pl) * G + g;
+            cp_async<Real>(sf + pl * PS + ti, fin + ga);
+            if (p.stage != 1 && b < 0) cp_async<Real>(sf0 + pl * Np + i, f0 + ga);
+          }
+        }
+      }
+    }
+    if (!AFFINE) {
+      for (int i = tid; i < Np; i += T) {
+        const Real *gm = p.drdx + ((size_t)e * Np + i) * DIM * DIM;
+#pragma unroll
+        for (int c = 0; c < DIM * DIM; ++c) sgeo[i * GEO + c] = -Bdt * gm[c];
+        sgeo[i * GEO + DIM * DIM] = p.wJ[(size_t)e * Np + i];
+      }
+    }
+    cp_async_wait_all();
+  }
+  __syncthreads();
+
+  // ---- flux bounce-back terms of the group's populations at this element's wall nodes
+  //      (Sec. 2.2.1); the opposite population comes from the unique-node array
+  const int w0 = p.wall_off[e], nw = p.wall_off[e + 1] - w0;
+  for (int idx = tid; idx < na * nw; idx += T) {
+    const int k = idx / na, pl = idx - k * na;
+    const int a = a0 + pl;
+    const WallPt<Real> &wp = p.walls[w0 + k];
+    const int ti = TI::node(wp.i);
+    const size_t g = l2g[wp.i];
+    Real sum = 0;
+    static_for<0, Q>([&](auto ac) {
+      constexpr int aa = decltype(ac)::value;
+      if (aa == a) {
+        constexpr int oa = V.opp[aa];
+        const Real fo = p.fin[(size_t)oa * G + g];
+        for (int f = 0; f < wp.nf; ++f) {
+          Real ne = 0, eu = 0;
+          const Real *ub = p.wall_u + 3 * (wp.wid[f] - 1);
+#pragma unroll
+          for (int k2 = 0; k2 < DIM; ++k2) {
+            if (V.e[aa][k2] > 0) { ne += wp.n[f][k2]; eu += ub[k2]; }
+            else if (V.e[aa][k2] < 0) { ne -= wp.n[f][k2]; eu -= ub[k2]; }
+          }
+          if (ne < Real(0)) {
+            const Real jump = sf[pl * PS + ti] - fo - Real(2) * Real(V.t[aa]) * p.rho0 * eu * Real(3);
+            sum += wp.wsJs[f] * ne * jump;
+          }
+        }
+      }
+    });
+    wbuf[k * PB + pl] = Bdt * sum;
+  }
+
+  // ---- one (population, r-line) task per thread
+  {
+    const int pl = tid / NL, L = tid - pl * NL;
+    const bool active = pl < na;
+    const int a = a0 + (active ? pl : 0);
+    const Real Je = AFFINE ? p.el_J[e] : Real(0);
+    const int i1 = L % n, i2 = L / n;
+    int yq[4], zq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      yq[q] = TI::SW ? i2 * TI::PL + ((q ^ (i2 & 3)) << 3) : i2 * TI::PL;
+      zq[q] = TI::SW ? ((i1 ^ q) << 3) : i1 * n;
+    }
+    auto yline = [&](int k) -> int { return TI::SW ? yq[k & 3] + ((k & 4) << 3) : yq[0] + k * n; };
+    auto zline = [&](int k) -> int { return TI::SW ? k * TI::PL + zq[k & 3] : k * TI::PL + zq[0]; };
+    const int zswz = TI::sw(i1);
+    const Real *sDi1 = sD + i1 * n, *sDi2 = sD + i2 * n;
+    const Real Jwl = Je * sw[i1] * sw[i2];
+    const bool edge_line = i1 == 0 || i1 == n - 1 || i2 == 0 || i2 == n - 1;
+    const int own = TI::line(i1, i2), own_swz = TI::sw(i1);
+    Real res[n];
+    if (active) {
+      const Real *fa = sf + pl * PS;
+      Real v[n];
+      load_line<Real, n>(fa + own, own_swz, v);
+      Real adv[n];
+#pragma unroll
+      for (int j = 0; j < n; ++j) adv[j] = 0;
+      if (AFFINE) {
+        const Real c0 = scoef[pl * DIM + 0], c1 = scoef[pl * DIM + 1], c2 = scoef[pl * DIM + 2];
+        if (c0 != Real(0)) {
+#pragma unroll
+          for (int j = 0; j < n; ++j) {
+            Real d = 0;
+#pragma unroll
+            for (int k = 0; k < n; ++k) d += m.D[j * n + k] * v[k];
+            adv[j] = c0 * d;
+          }
+        }
+        if (c1 != Real(0)) {
+#pragma unroll KU
+          for (int k = 0; k < n; ++k) {
+            const Real s = c1 * sDi1[k];
+            Real w[n];
+            load_line<Real, n>(fa + yline(k), TI::sw(k), w);
+#pragma unroll
+            for (int j = 0; j < n; ++j) adv[j] += s * w[j];
+          }
+        }
+        if (c2 != Real(0)) {
+#pragma unroll KU
+          for (int k = 0; k < n; ++k) {
+            const Real s = c2 * sDi2[k];
+            Real w[n];
+            load_line<Real, n>(fa + zline(k), zswz, w);
+#pragma unroll
+            for (int j = 0; j < n; ++j) adv[j] += s * w[j];
+          }
+        }
+      } else {
+        // curved elements: adv = sum_l c_l d_l with c_l = sum_k e_k (-B dt dr_l/dx_k) per node
+        int ek[3] = {0, 0, 0};
+        static_for<0, Q>([&](auto ac) {
+          constexpr int aa = decltype(ac)::value;
+          if (aa == a) { ek[0] = V.e[aa][0]; ek[1] = V.e[aa][1]; ek[2] = V.e[aa][2]; }
+        });
+        auto coef = [&](int j, int l) -> Real {
+          const Real *gm = sgeo + (L * n + j) * GEO + l * DIM;
+          Real c = 0;
+#pragma unroll
+          for (int k = 0; k < DIM; ++k)
+            if (ek[k] != 0) c += ek[k] > 0 ? gm[k] : -gm[k];
+          return c;
+        };
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          Real d = 0;
+#pragma unroll
+          for (int k = 0; k < n; ++k) d += m.D[j * n + k] * v[k];
+          adv[j] = coef(j, 0) * d;
+        }
+        {
+          Real d[n];
+#pragma unroll
+          for (int j = 0; j < n; ++j) d[j] = 0;
+#pragma unroll KU
+          for (int k = 0; k < n; ++k) {
+            const Real s = sDi1[k];
+            Real w[n];
+            load_line<Real, n>(fa + yline(k), TI::sw(k), w);
+#pragma unroll
+            for (int j = 0; j < n; ++j) d[j] += s * w[j];
+          }
+#pragma unroll
+          for (int j = 0; j < n; ++j) adv[j] += coef(j, 1) * d[j];
+        }
+        {
+          Real d[n];
+#pragma unroll
+          for (int j = 0; j < n; ++j) d[j] = 0;
+#pragma unroll KU
+          for (int k = 0; k < n; ++k) {
+            const Real s = sDi2[k];
+            Real w[n];
+            load_line<Real, n>(fa + zline(k), zswz, w);
+#pragma unroll
+            for (int j = 0; j < n; ++j) d[j] += s * w[j];
+          }
+#pragma unroll
+          for (int j = 0; j < n; ++j) adv[j] += coef(j, 2) * d[j];
+        }
+      }
+      // element-interior nodes: B f^{s-1} + (-B dt) e.grad f (A f^0 and B dt F* added on output);
+      // element-boundary nodes: weighted share wJ (-B dt) e.grad f for the assembly
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        const bool bnd = edge_line || j == 0 || j == n - 1;
+        if (!bnd) {
+          res[j] = p.B * v[j] + adv[j];
+        } else {
+          const Real wJ = AFFINE ? Jwl * m.w[j] : sgeo[(L * n + j) * GEO + DIM * DIM];
+          res[j] = wJ * adv[j];
+        }
+      }
+    }
+    __syncthreads();
+    if (active) store_line<Real, n>(sf + pl * PS + own, own_swz, res);
+  }
+  __syncthreads();
+
+  // ---- outputs, one node per thread with the group's populations (coalesced across the
+  //      warp for each population)
+  {
+    Real *__restrict__ fout = p.fout;
+    Real *__restrict__ Tr = p.T;
+    const size_t EN = (size_t)p.E * p.Nb;
+#pragma unroll
+    for (int r = 0; r < NPT; ++r) {
+      const int i = tid + r * T;
+      if (i < Np) {
+        const int ti = TI::node(i);
+        const int b = p.bslot[i];
+        if (b < 0) {
+          const int g = l2g[i];
+          const Real rg = p.has_force ? p.rho[g] : Real(0);
+          Real *fo = fout + g;
+#pragma unroll
+          for (int pl = 0; pl < PB; ++pl) {
+            if (pl < na) {
+              Real out = sf[pl * PS + ti];
+              if (p.stage != 1) out += p.A * sf0[pl * Np + i];
+              if (p.has_force) out += sfc[pl] * rg;
+              fo[(size_t)(a0 + pl) * G] = out;
+            }
+          }
+        } else {
+          Real *tp = Tr + (size_t)e * p.Nb + b;
+#pragma unroll
+          for (int pl = 0; pl < PB; ++pl)
+            if (pl < na) tp[(size_t)(a0 + pl) * EN] = sf[pl * PS + ti];
+        }
+      }
+    }
+  }
+  if (nw > 0) {
+    __syncthreads();
+    const size_t EN = (size_t)p.E * p.Nb;
+    for (int idx = tid; idx < na * nw; idx += T) {
+      const int k = idx / na, pl = idx - k * na;
+      p.T[(size_t)(a0 + pl) * EN + (size_t)e * p.Nb + p.walls[w0 + k].b] += wbuf[k * PB + pl];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// prologue: pending filter + collision, one CTA per element with all Q populations
+// ---------------------------------------------------------------------------
+// learned control inputs of the prologue (network: 2n -> 64 tanh -> 64 tanh -> 2)
+template <typename Real, int n>
+struct LearnedIn {
+  Real Vm[n * n];               // modal -> nodal
+  Real Vinv[n * n];             // nodal -> modal
+  Real fixed_sigma[n];          // transfer function of the fixed filter (fallback)
+  const __nv_bfloat16 *W;       // parameters; NULL = features only
+  const Real *lo, *hi;          // [2n] training range of the features
+  const int *flag;              // sticky drift fallback flag or NULL
+  double *acc;                  // drift accumulators (mass, KE) or NULL
+  Real *sigma_out;              // [E][n] or NULL
+  float *feat_out;              // [E][2n] or NULL
+  int *n_fallback;              // counter of elements that kept the fixed filter, or NULL
+  int outputs;                  // 0: features / transfer functions only
+};
+
+constexpr int kProThreads = 256;
+constexpr int kHidden = 64;
+
+template <typename Real, int LAT, int n, bool AFFINE, int MODE>
+constexpr size_t prologue_smem_bytes() {
+  using TI = Tile<Real, n, 3>;
+  constexpr int Q = LT<LAT>::v.Q;
+  size_t reals = (size_t)Q * TI::PS + 2 * n * n;                   // tile; U, W or F_e, V^-1
+  if (MODE == PRO_LEARNED)
+    reals += 2 * (size_t)TI::PS + n * n + n + 2 * n + 2 * kHidden + 2 + (kProThreads / 32) * 2 * n;
+  return reals * sizeof(Real);
+}
+
+// y <- (A x A x A) y on NP populations of a tile, one 1D pass per axis; op maps the n
+// values of one line in place
+template <typename Real, int n, int NP, int T, typename Op>
+__device__ __forceinline__ void tile_pass3(Real *sf, int tid, Op op) {
+  using TI = Tile<Real, n, 3>;
+  constexpr int NL = n * n, PS = TI::PS;
+  for (int t = tid; t < NP * NL; t += T) {          // r-lines
+    const int a = t / NL, L = t - a * NL;
+    const int i1 = L % n, i2 = L / n;
+    Real v[n];
+    Real *base = sf + a * PS + TI::line(i1, i2);
+    load_line<Real, n>(base, TI::sw(i1), v);
+    op(v);
+    store_line<Real, n>(base, TI::sw(i1), v);
+  }
+  __syncthreads();
+  for (int t = tid; t < NP * NL; t += T) {          // s-lines
+    const int a = t / NL, r = t - a * NL, i0 = r % n, i2 = r / n;
+    Real v[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) v[k] = sf[a * PS + TI::at(i0, k, i2)];
+    op(v);
+#pragma unroll
+    for (int k = 0; k < n; ++k) sf[a * PS + TI::at(i0, k, i2)] = v[k];
+  }
+  __syncthreads();
+  for (int t = tid; t < NP * NL; t += T) {          // t-lines
+    const int a = t / NL, r = t - a * NL, i0 = r % n, i1 = r / n;
+    Real v[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) v[k] = sf[a * PS + TI::at(i0, i1, k)];
+    op(v);
+#pragma unroll
+    for (int k = 0; k < n; ++k) sf[a * PS + TI::at(i0, i1, k)] = v[k];
+  }
+  __syncthreads();
+}
+
+template <typename Real, int n>
+__device__ __forceinline__ void dense_vals(Real (&v)[n], const Real *M) {
+  Real o[n];
+#pragma unroll
+  for (int j = 0; j < n; ++j) {
+    Real s = 0;
+#pragma unroll
+    for (int k = 0; k < n; ++k) s += M[j * n + k] * v[k];
+    o[j] = s;
+  }
+#pragma unroll
+  for (int j = 0; j < n; ++j) v[j] = o[j];
+}
+
+template <typename Real, int LAT, int n, bool AFFINE, int MODE>
+__global__ void __launch_bounds__(kProThreads)
+prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedIn<Real, n> c) {
+  constexpr int Q = LT<LAT>::v.Q, DIM = 3, Np = n * n * n, T = kProThreads, NW = T / 32, H = kHidden, nin = 2 * n;
+  using TI = Tile<Real, n, DIM>;
+  constexpr int PS = TI::PS;
+  constexpr VelTab V = LT<LAT>::v;
+  constexpr bool LEARNED = MODE == PRO_LEARNED;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real *sf = reinterpret_cast<Real *>(smem_raw);   // [Q][PS]
+  Real *sM0 = sf + Q * PS;                          // [n][n] U (fixed) or F_e (learned)
+  Real *sM1 = sM0 + n * n;                          // [n][n] W (fixed) or V^-1 (learned)
+  Real *sq = sM1 + n * n;                           // learned: [2][PS] rho - rho0, |u| -> modal
+  Real *sVm = sq + 2 * PS;                          // [n][n]
+  Real *ssig = sVm + n * n;                         // [n]
+  Real *sx = ssig + n;                              // [2n]
+  Real *h1 = sx + nin;                              // [64]
+  Real *h2 = h1 + H;                                // [64]
+  Real *so = h2 + H;                                // [2]
+  Real *spart = so + 2;                             // [NW][2n]
+  __shared__ double dred[NW][2];
+  __shared__ int s_r, in_range;
+  const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int32_t *l2g = p.l2g + (size_t)e * Np;
+  const size_t G = p.G;
+  auto weight = [&](int i) -> Real {
+    if (AFFINE) {
+      const int i0 = i % n, i1 = (i / n) % n, i2 = i / (n * n);
+      return p.el_J[e] * p.gllw[i0] * p.gllw[i1] * p.gllw[i2];
+    }
+    return p.wJ[(size_t)e * Np + i];
+  };
+  if (MODE == PRO_FIXED) {
+    for (int k = tid; k < n * n; k += T) { sM0[k] = m.U[k]; sM1[k] = m.W[k]; }
+    if (tid == 0) s_r = m.r;
+  }
+  if (LEARNED) {
+    for (int k = tid; k < n * n; k += T) { sM1[k] = c.Vinv[k]; sVm[k] = c.Vm[k]; }
+    if (tid == 0) in_range = 1;
+  }
+  // ---- gather; the learned control also takes rho - rho0 and |u| at every node
+  double pm = 0.0, pk = 0.0;
+  {
+    const Real *__restrict__ fin = p.fin;
+    for (int i = tid; i < Np; i += T) {
+      const size_t g = l2g[i];
+      const int ti = TI::node(i);
+      Real drho = 0, j[3] = {0, 0, 0};
+      static_for<0, Q>([&](auto ac) {
+        constexpr int a = decltype(ac)::value;
+        const Real v = fin[(size_t)a * G + g];
+        sf[a * PS + ti] = v;
+        if (LEARNED) {
+          drho += v;
+#pragma unroll
+          for (int k = 0; k < DIM; ++k) {
+            if (V.e[a][k] > 0) j[k] += v;
+            else if (V.e[a][k] < 0) j[k] -= v;
+          }
+        }
+      });
+      if (LEARNED) {
+        const Real rho = p.rho0 + drho;
+        Real uu = 0;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) uu += (j[k] / rho) * (j[k] / rho);
+        sq[ti] = drho;
+        sq[PS + ti] = sqrt(uu);
+        if (c.acc) {
+          const double wq = (double)weight(i);
+          pm += wq * (double)rho;
+          pk += 0.5 * (double)p.rho0 * wq * (double)uu;
+        }
+      }
+    }
+  }
+  if (LEARNED && c.acc) {
+    pm = warp_sum(pm);
+    pk = warp_sum(pk);
+    if (lane == 0) { dred[wid][0] = pm; dred[wid][1] = pk; }
+  }
+  __syncthreads();
+
+  if (LEARNED) {
+    if (c.acc && tid == 0) {
+      double sm = 0.0, sk = 0.0;
+      for (int w = 0; w < NW; ++w) { sm += dred[w][0]; sk += dred[w][1]; }
+      atomicAdd(&c.acc[0], sm);
+      atomicAdd(&c.acc[1], sk);
+    }
+    // modal coefficients of both fields: V^-1 along every axis
+    tile_pass3<Real, n, 2, T>(sq, tid, [&](Real (&v)[n]) { dense_vals<Real, n>(v, sM1); });
+    // shell energies E_k = sum over max(k0, k1, k2) = k of the squared coefficients
+    Real en[2][n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) { en[0][k] = 0; en[1][k] = 0; }
+    for (int i = tid; i < Np; i += T) {
+      const int i0 = i % n, i1 = (i / n) % n, i2 = i / (n * n);
+      const int sh = max(i0, max(i1, i2));
+      const int ti = TI::node(i);
+      const Real q0 = sq[ti], q1 = sq[PS + ti];
+#pragma unroll
+      for (int k = 0; k < n; ++k)
+        if (k == sh) { en[0][k] += q0 * q0; en[1][k] += q1 * q1; }
+    }
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        const Real s = warp_sum(en[f][k]);
+        if (lane == 0) spart[wid * nin + f * n + k] = s;
+      }
+    __syncthreads();
+    if (tid < nin) {
+      Real s = 0;
+      for (int w = 0; w < NW; ++w) s += spart[w * nin + tid];
+      const Real x = log10(s + Real(1e-30));
+      if (c.feat_out) c.feat_out[(size_t)e * nin + tid] = (float)x;
+      if (c.W) {
+        const Real lo = c.lo[tid], hi = c.hi[tid];
+        if (!(x >= lo && x <= hi)) in_range = 0;
+        sx[tid] = Real(2) * (x - lo) / (hi - lo) - Real(1);
+      }
+    }
+    if (!c.W) return;
+    __syncthreads();
+    const bool use_net = in_range && !(c.flag && *c.flag);
+    if (use_net) {
+      const __nv_bfloat16 *W1 = c.W, *b1 = W1 + H * nin, *W2 = b1 + H, *b2 = W2 + H * H, *W3 = b2 + H, *b3 = W3 + 2 * H;
+      for (int o = wid; o < H; o += NW) {
+        Real z = lane < nin ? (Real)__bfloat162float(W1[o * nin + lane]) * sx[lane] : Real(0);
+        z = warp_sum(z);
+        if (lane == 0) h1[o] = tanh((Real)__bfloat162float(b1[o]) + z);
+      }
+      __syncthreads();
+      for (int o = wid; o < H; o += NW) {
+        const __nv_bfloat162 w2 = reinterpret_cast<const __nv_bfloat162 *>(W2 + o * H)[lane];
+        Real z = (Real)__low2float(w2) * h1[2 * lane] + (Real)__high2float(w2) * h1[2 * lane + 1];
+        z = warp_sum(z);
+        if (lane == 0) h2[o] = tanh((Real)__bfloat162float(b2[o]) + z);
+      }
+      __syncthreads();
+      if (wid < 2) {
+        const __nv_bfloat162 w3 = reinterpret_cast<const __nv_bfloat162 *>(W3 + wid * H)[lane];
+        Real z = (Real)__low2float(w3) * h2[2 * lane] + (Real)__high2float(w3) * h2[2 * lane + 1];
+        z = warp_sum(z);
+        if (lane == 0) so[wid] = (Real)__bfloat162float(b3[wid]) + z;
+      }
+      __syncthreads();
+    } else if (tid == 0 && c.n_fallback) {
+      atomicAdd(c.n_fallback, 1);
+    }
+    if (tid < n) {
+      Real sig = c.fixed_sigma[tid];
+      if (use_net) {
+        const Real gam = Real(0.5) / (Real(1) + exp(-so[0]));
+        const Real kc = Real(2) + Real(n - 4) / (Real(1) + exp(-so[1]));
+        sig = Real(1);
+        if (tid > kc) {
+          const Real r = (Real(tid) - kc) / (Real(n - 1) - kc);
+          sig = Real(1) - gam * r * r;
+        }
+      }
+      ssig[tid] = sig;
+      if (c.sigma_out) c.sigma_out[(size_t)e * n + tid] = sig;
+    }
+    if (!c.outputs) return;
+    __syncthreads();
+    // F_e = V diag(sigma) V^-1 with exact identity end rows
+    for (int k = tid; k < n * n; k += T) {
+      const int r = k / n, jj = k - r * n;
+      Real s = 0;
+#pragma unroll
+      for (int q = 0; q < n; ++q) s += sVm[r * n + q] * ssig[q] * sM1[q * n + jj];
+      if (r == 0 || r == n - 1) s = (r == jj) ? Real(1) : Real(0);
+      sM0[k] = s;
+    }
+    __syncthreads();
+    tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { dense_vals<Real, n>(v, sM0); });
+  } else if (MODE == PRO_FIXED) {
+    const int r = s_r;
+    tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { filter_vals<Real, n>(v, sM0, sM1, r); });
+  }
+
+  // ---- collision at every node this element writes: owned copies (one filter for
+  //      all elements, so copies agree), or element-interior nodes with the learned
+  //      control, whose element-boundary copies go to the trace as wJ f for the
+  //      mass-weighted assembly of shared nodes
+  const Real gacc[3] = {p.g[0], p.g[1], p.g[2]};
+  const size_t EN = (size_t)p.E * p.Nb;
+  for (int i = tid; i < Np; i += T) {
+    const int ti = TI::node(i);
+    const size_t g = l2g[i];
+    if (LEARNED) {
+      const int b = p.bslot[i];
+      if (b >= 0) {
+        const Real wq = weight(i);
+        Real *tp = p.T + (size_t)e * p.Nb + b;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) tp[a * EN] = wq * sf[a * PS + ti];
+        continue;
+      }
+    } else if (!p.owner[(size_t)e * Np + i]) {
+      continue;
+    }
+    Real fr[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) fr[a] = sf[a * PS + ti];
+    const Real rho = bgk_collide<Real, LAT>(fr, p.rho0, p.omega, p.dt, p.half_dt, gacc, p.has_force != 0);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) p.f0out[(size_t)a * G + g] = fr[a];
+    if (p.has_force) p.rho[g] = rho;
+  }
+}
+
+// mass-weighted assembly of the learned control's filtered copies at shared nodes,
+// then the collision there
+template <typename Real, int LAT>
+__global__ void __launch_bounds__(256) dss_collide_kernel(const KParams<Real> p) {
+  constexpr int Q = LT<LAT>::v.Q;
+  const size_t EN = (size_t)p.E * p.Nb;
+  const Real gacc[3] = {p.g[0], p.g[1], p.g[2]};
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < p.Gb; u += gridDim.x * blockDim.x) {
+    const int c0 = p.bnode_off[u], c1 = p.bnode_off[u + 1];
+    const size_t gid = p.bnode_g[u];
+    const Real minv = p.bnode_minv[u];
+    Real s[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) s[a] = 0;
+    for (int k = c0; k < c1; ++k) {
+      const Real *tc = p.T + p.bnode_slot[k];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) s[a] += tc[a * EN];
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a) s[a] *= minv;
+    const Real rho = bgk_collide<Real, LAT>(s, p.rho0, p.omega, p.dt, p.half_dt, gacc, p.has_force != 0);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) p.f0out[(size_t)a * p.G + gid] = s[a];
+    if (p.has_force) p.rho[gid] = rho;
+  }
+}
+
+// collision on unique nodes (no pending filter)
+template <typename Real, int LAT>
+__global__ void __launch_bounds__(256) collide_nodes_kernel(const KParams<Real> p) {
+  constexpr int Q = LT<LAT>::v.Q;
+  const Real gacc[3] = {p.g[0], p.g[1], p.g[2]};
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < (size_t)p.G; g += (size_t)gridDim.x * blockDim.x) {
+    Real s[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) s[a] = p.fin[(size_t)a * p.G + g];
+    const Real rho = bgk_collide<Real, LAT>(s, p.rho0, p.omega, p.dt, p.half_dt, gacc, p.has_force != 0);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) p.f0out[(size_t)a * p.G + g] = s[a];
+    if (p.has_force) p.rho[g] = rho;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <typename Real, int n>
+FastMats<Real, n> make_fast_mats(const SplitHost &h) {
+  FastMats<Real, n> m{};
+  for (int k = 0; k < n * n; ++k) { m.D[k] = (Real)h.D[k]; m.U[k] = (Real)h.U[k]; m.W[k] = (Real)h.W[k]; }
+  for (int k = 0; k < n; ++k) m.w[k] = (Real)h.w[k];
+  m.r = h.r;
+  return m;
+}
+
+// sets the kernel's dynamic shared-memory limit once per device (per instantiation)
+#define SLB_SET_SMEM_ONCE(kernel, smem)                                                          \
+  do {                                                                                           \
+    static thread_local int attr_dev_ = -1;                                                      \
+    static thread_local size_t attr_smem_ = 0;                                                   \
+    int dev_ = 0;                                                                                \
+    cudaGetDevice(&dev_);                                                                        \
+    if (attr_dev_ != dev_ || attr_smem_ < (smem)) {                                              \
+      cudaError_t err_ = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem)); \
+      if (err_ != cudaSuccess) return err_;                                                      \
+      attr_dev_ = dev_;                                                                          \
+      attr_smem_ = (smem);                                                                       \
+    }                                                                                            \
+  } while (0)
+
+template <typename Real, int LAT, int n, bool AFFINE>
+cudaError_t launch_split_t(const KParams<Real> &p, const SplitHost &h, cudaStream_t s) {
+  using S = SplitShape<LAT, n>;
+  const size_t smem = split_smem_bytes<Real, LAT, n, AFFINE>(p.wall_max);
+  auto k = stage_split_kernel<Real, LAT, n, AFFINE>;
+  SLB_SET_SMEM_ONCE(k, smem);
+  k<<<p.E * S::NG, S::THREADS, smem, s>>>(p, make_fast_mats<Real, n>(h));
+  return cudaGetLastError();
+}
+
+template <typename Real, int LAT, int n, bool AFFINE, int MODE>
+cudaError_t launch_prologue_t(const KParams<Real> &p, const SplitHost &h, const LearnedPtrs<Real> &lp, cudaStream_t s) {
+  LearnedIn<Real, n> c{};
+  if (MODE == PRO_LEARNED) {
+    for (int k = 0; k < n * n; ++k) { c.Vm[k] = (Real)h.Vm[k]; c.Vinv[k] = (Real)h.Vinv[k]; }
+    for (int k = 0; k < n; ++k) c.fixed_sigma[k] = (Real)h.fixed_sigma[k];
+    c.W = lp.W; c.lo = lp.lo; c.hi = lp.hi; c.flag = lp.flag; c.acc = lp.acc; c.sigma_out = lp.sigma_out;
+    c.feat_out = lp.feat_out; c.n_fallback = lp.n_fallback; c.outputs = lp.outputs;
+  }
+  const size_t smem = prologue_smem_bytes<Real, LAT, n, AFFINE, MODE>();
+  auto k = prologue_kernel<Real, LAT, n, AFFINE, MODE>;
+  SLB_SET_SMEM_ONCE(k, smem);
+  k<<<p.E, kProThreads, smem, s>>>(p, make_fast_mats<Real, n>(h), c);
+  return cudaGetLastError();
+}
+
+template <typename Real, int LAT>
+cudaError_t launch_dss_collide_t(const KParams<Real> &p, cudaStream_t s) {
+  if (p.Gb == 0) return cudaSuccess;
+  const int threads = 256;
+  const int blocks = (int)std::min<size_t>(((size_t)p.Gb + threads - 1) / threads, 152 * 32);
+  dss_collide_kernel<Real, LAT><<<blocks, threads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename Real, int LAT>
+cudaError_t launch_collide_nodes_t(const KParams<Real> &p, cudaStream_t s) {
+  const int threads = 256;
+  const int blocks = (int)std::min<size_t>(((size_t)p.G + threads - 1) / threads, 152 * 32);
+  collide_nodes_kernel<Real, LAT><<<blocks, threads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace slb
