@@ -20,6 +20,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "selbm_collide.cuh"
 #include "selbm_fast.cuh"
 
@@ -38,10 +40,11 @@ template <int LAT, int n>
 struct SplitShape {
   static constexpr int Q = LT<LAT>::v.Q;
   static constexpr int Np = n * n * n, NL = n * n;
-  static constexpr int PB = (256 / NL) < 1 ? 1 : (256 / NL);     // populations per CTA
-  static constexpr int THREADS = PB * NL;                         // one (population, r-line) task each
-  static constexpr int NG = (Q + PB - 1) / PB;                    // CTAs per element
-  static constexpr int GEO = 10;
+  static constexpr int LPR = 256 / NL < 1 ? 1 : 256 / NL;         // populations per round of tasks
+  static constexpr int THREADS = LPR * NL;                        // one (population, r-line) task per round
+  static constexpr int ROUNDS = 2;
+  static constexpr int PB = ROUNDS * LPR;                         // populations per work item
+  static constexpr int NG = (Q + PB - 1) / PB;                    // work items per element
   static constexpr int NPT = (Np + THREADS - 1) / THREADS;        // nodes per thread when gathering
 };
 
@@ -49,10 +52,46 @@ template <typename Real, int LAT, int n, bool AFFINE>
 constexpr size_t split_smem_bytes(int wall_max) {
   using S = SplitShape<LAT, n>;
   using TI = Tile<Real, n, 3>;
-  size_t reals = (size_t)S::PB * TI::PS + n * n + S::PB * 3 + S::PB + n + (size_t)S::PB * S::Np;
-  if (!AFFINE) reals += (size_t)S::Np * S::GEO;
+  size_t reals = 2 * (size_t)S::PB * TI::PS + n * n + S::PB * 3 + S::PB + n;
+  if (!AFFINE) reals += (size_t)S::Np * 10;
   reals += (size_t)S::PB * wall_max;
   return reals * sizeof(Real);
+}
+
+// bit a of pos_mask(k) (neg_mask(k)) is set when population a has e_k = +1 (-1)
+constexpr uint32_t vel_mask(const VelTab &v, int k, int sgn) {
+  uint32_t m = 0;
+  for (int a = 0; a < v.Q; ++a)
+    if (v.e[a][k] == sgn) m |= 1u << a;
+  return m;
+}
+template <typename Real>
+__device__ __forceinline__ Real mask_sign(uint32_t pos, uint32_t neg, int a) {
+  return Real((int)((pos >> a) & 1u) - (int)((neg >> a) & 1u));
+}
+
+// acc[j] += s * w[j], j < n (packed FP32 pairs where the type allows)
+template <typename Real, int n>
+__device__ __forceinline__ void axpy_line(Real (&acc)[n], Real s, const Real (&w)[n]) {
+  if constexpr (sizeof(Real) == 4 && n % 2 == 0) {
+    const float2 ss = make_float2(s, s);
+#pragma unroll
+    for (int j = 0; j < n; j += 2) {
+      const float2 r = __ffma2_rn(ss, make_float2(w[j], w[j + 1]), make_float2(acc[j], acc[j + 1]));
+      acc[j] = r.x;
+      acc[j + 1] = r.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < n; ++j) acc[j] += s * w[j];
+  }
+}
+
+// asynchronous copy of one value to a shared-memory byte address
+template <typename Real>
+__device__ __forceinline__ void cp_async_s(unsigned dst, const Real *src) {
+  if constexpr (sizeof(Real) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -63,84 +102,98 @@ __global__ void __launch_bounds__(SplitShape<LAT, n>::THREADS, (sizeof(Real) == 
 stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   using S = SplitShape<LAT, n>;
   constexpr int Q = S::Q, DIM = 3, Np = S::Np, NL = S::NL, T = S::THREADS, PB = S::PB, NG = S::NG;
-  constexpr int GEO = S::GEO, NPT = S::NPT;
+  constexpr int NPT = S::NPT, LPR = S::LPR, ROUNDS = S::ROUNDS;
   using TI = Tile<Real, n, DIM>;
   constexpr int PS = TI::PS;
   constexpr VelTab V = LT<LAT>::v;
+  constexpr uint32_t POS[3] = {vel_mask(V, 0, 1), vel_mask(V, 1, 1), vel_mask(V, 2, 1)};
+  constexpr uint32_t NEG[3] = {vel_mask(V, 0, -1), vel_mask(V, 1, -1), vel_mask(V, 2, -1)};
   constexpr int KU = sizeof(Real) == 4 ? n : 2;
+  constexpr unsigned RS = sizeof(Real);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real *sf = reinterpret_cast<Real *>(smem_raw);   // [PB][PS] tile of the group
-  Real *sD = sf + PB * PS;                          // [n][n]
-  Real *scoef = sD + n * n;                         // [PB][DIM] (affine: -B dt sum_k e_k dr_l/dx_k)
-  Real *sfc = scoef + PB * DIM;                     // [PB]      B dt F*_a / rho
-  Real *sw = sfc + PB;                              // [n]
-  Real *sgeo = sw + n;                              // [Np][GEO] (curved: -B dt dr_l/dx_k, wJ)
-  Real *sf0 = sgeo + (AFFINE ? 0 : Np * GEO);       // [PB][Np] f^0 of element-interior nodes
-  Real *wbuf = sf0 + PB * Np;                       // [wall nodes][PB]
+  Real *sf = reinterpret_cast<Real *>(smem_raw);   // [PB][PS] f^{s-1} of the group
+  Real *so = sf + PB * PS;                          // [PB][PS] f^0 in, stage result out
+  Real *sD = so + PB * PS;                          // [n][n]
+  Real *cf = sD + n * n;                            // [PB][DIM] (affine: -B dt sum_k e_k dr_l/dx_k)
+  Real *fc = cf + PB * DIM;                         // [PB]      B dt F*_a / rho
+  Real *sw = fc + PB;                               // [n]
+  Real *sg = sw + n;                                // curved: dr_l/dx_k [Np][9], wJ [Np]
+  Real *wbuf = sg + (AFFINE ? 0 : Np * 10);         // [wall nodes][PB]
   const int e = blockIdx.x / NG, a0 = (blockIdx.x - e * NG) * PB;
   const int na = Q - a0 < PB ? Q - a0 : PB;
+  const bool full = na == PB;
   const int tid = threadIdx.x;
   const Real Bdt = p.B * p.dt;
   const int32_t *l2g = p.l2g + (size_t)e * Np;
   const size_t G = p.G;
+  const bool use_f0 = p.stage != 1;
 
-  for (int k = tid; k < n * n; k += T) sD[k] = m.D[k];
-  if (tid < n) sw[tid] = m.w[tid];
-  if (tid < na) {
-    const int a = a0 + tid;
-    static_for<0, Q>([&](auto ac) {
-      constexpr int aa = decltype(ac)::value;
-      if (aa == a) {
-        if (AFFINE) {
-#pragma unroll
-          for (int l = 0; l < DIM; ++l) {
-            Real c = 0;
-#pragma unroll
-            for (int k = 0; k < DIM; ++k)
-              if (V.e[aa][k] != 0) c += (V.e[aa][k] > 0 ? Real(1) : Real(-1)) * p.el_drdx[((size_t)e * DIM + l) * DIM + k];
-            scoef[tid * DIM + l] = -Bdt * c;
-          }
-        }
-        Real ge = 0;
-#pragma unroll
-        for (int k = 0; k < DIM; ++k)
-          if (V.e[aa][k] != 0) ge += (V.e[aa][k] > 0 ? Real(1) : Real(-1)) * p.g[k];
-        sfc[tid] = Bdt * Real(V.t[aa]) * Real(3) * ge;
-      }
-    });
-  }
-  // ---- gather the group's tile, and f^0 of element-interior nodes for the output,
-  //      with asynchronous copies (no register staging, all of them in flight at once)
+  // ---- gather f^{s-1} of the group (and f^0 of element-interior nodes) with asynchronous
+  //      copies: no register staging, all of them in flight at once
   {
-    const Real *fin = p.fin;
-    const Real *f0 = p.f0;
+    const unsigned s_f = (unsigned)__cvta_generic_to_shared(sf), s_o = (unsigned)__cvta_generic_to_shared(so);
+    const Real *fin = p.fin + (size_t)a0 * G;
+    const Real *f0 = p.f0 + (size_t)a0 * G;
 #pragma unroll
     for (int r = 0; r < NPT; ++r) {
       const int i = tid + r * T;
       if (i < Np) {
         const int g = l2g[i];
-        const int b = p.bslot[i];
-        const int ti = TI::node(i);
+        const bool f0n = use_f0 && p.bslot[i] < 0;
+        const unsigned ti = TI::node(i) * RS;
+        const Real *src = fin + g, *src0 = f0 + g;
+        if (full) {
 #pragma unroll
-        for (int pl = 0; pl < PB; ++pl) {
-          if (pl < na) {
-            const size_t ga = (size_t)(a0 + pl) * G + g;
-            cp_async<Real>(sf + pl * PS + ti, fin + ga);
-            if (p.stage != 1 && b < 0) cp_async<Real>(sf0 + pl * Np + i, f0 + ga);
+          for (int pl = 0; pl < PB; ++pl) cp_async_s<Real>(s_f + ti + pl * PS * RS, src + pl * G);
+          if (f0n) {
+#pragma unroll
+            for (int pl = 0; pl < PB; ++pl) cp_async_s<Real>(s_o + ti + pl * PS * RS, src0 + pl * G);
+          }
+        } else {
+#pragma unroll
+          for (int pl = 0; pl < PB; ++pl) {
+            if (pl < na) {
+              cp_async_s<Real>(s_f + ti + pl * PS * RS, src + pl * G);
+              if (f0n) cp_async_s<Real>(s_o + ti + pl * PS * RS, src0 + pl * G);
+            }
           }
         }
       }
     }
     if (!AFFINE) {
-      for (int i = tid; i < Np; i += T) {
-        const Real *gm = p.drdx + ((size_t)e * Np + i) * DIM * DIM;
-#pragma unroll
-        for (int c = 0; c < DIM * DIM; ++c) sgeo[i * GEO + c] = -Bdt * gm[c];
-        sgeo[i * GEO + DIM * DIM] = p.wJ[(size_t)e * Np + i];
-      }
+      const unsigned s_g = (unsigned)__cvta_generic_to_shared(sg);
+      const Real *gm = p.drdx + (size_t)e * Np * 9;
+      for (int c = tid; c < Np * 9; c += T) cp_async_s<Real>(s_g + c * RS, gm + c);
+      const Real *wj = p.wJ + (size_t)e * Np;
+      for (int c = tid; c < Np; c += T) cp_async_s<Real>(s_g + (Np * 9 + c) * RS, wj + c);
     }
-    cp_async_wait_all();
   }
+  // ---- per-element constants while the copies are in flight
+  for (int k = tid; k < n * n; k += T) sD[k] = m.D[k];
+  if (tid < n) sw[tid] = m.w[tid];
+  if (AFFINE && tid < PB * DIM) {
+    const int pl = tid / DIM, l = tid - pl * DIM;
+    const int a = a0 + pl;
+    Real c = 0;
+    if (a < Q) {
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) c += mask_sign<Real>(POS[k], NEG[k], a) * p.el_drdx[((size_t)e * DIM + l) * DIM + k];
+    }
+    cf[tid] = -Bdt * c;
+  }
+  if (p.has_force && tid < na) {
+    const int a = a0 + tid;
+    Real ge = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) ge += mask_sign<Real>(POS[k], NEG[k], a) * p.g[k];
+    Real ta = 0;
+    static_for<0, Q>([&](auto ac) {
+      constexpr int aa = decltype(ac)::value;
+      if (aa == a) ta = Real(V.t[aa]);
+    });
+    fc[tid] = Bdt * ta * Real(3) * ge;
+  }
+  cp_async_wait_all();
   __syncthreads();
 
   // ---- flux bounce-back terms of the group's populations at this element's wall nodes
@@ -176,12 +229,11 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
     wbuf[k * PB + pl] = Bdt * sum;
   }
 
-  // ---- one (population, r-line) task per thread
+  // ---- (population, r-line) tasks, ROUNDS per thread with the same r-line (i1, i2);
+  //      a task reads f^{s-1} lines from sf and replaces its own line of so (f^0 in,
+  //      result out), which no other task touches
   {
-    const int pl = tid / NL, L = tid - pl * NL;
-    const bool active = pl < na;
-    const int a = a0 + (active ? pl : 0);
-    const Real Je = AFFINE ? p.el_J[e] : Real(0);
+    const int L = tid % NL;
     const int i1 = L % n, i2 = L / n;
     int yq[4], zq[4];
 #pragma unroll
@@ -193,11 +245,14 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
     auto zline = [&](int k) -> int { return TI::SW ? k * TI::PL + zq[k & 3] : k * TI::PL + zq[0]; };
     const int zswz = TI::sw(i1);
     const Real *sDi1 = sD + i1 * n, *sDi2 = sD + i2 * n;
-    const Real Jwl = Je * sw[i1] * sw[i2];
+    const Real *swj = sg + Np * 9;
+    const Real Jwl = AFFINE ? p.el_J[e] * sw[i1] * sw[i2] : Real(0);
     const bool edge_line = i1 == 0 || i1 == n - 1 || i2 == 0 || i2 == n - 1;
     const int own = TI::line(i1, i2), own_swz = TI::sw(i1);
-    Real res[n];
-    if (active) {
+#pragma unroll 1
+    for (int rd = 0; rd < ROUNDS; ++rd) {
+      const int pl = tid / NL + rd * LPR;
+      if (pl >= na) break;
       const Real *fa = sf + pl * PS;
       Real v[n];
       load_line<Real, n>(fa + own, own_swz, v);
@@ -205,7 +260,7 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
 #pragma unroll
       for (int j = 0; j < n; ++j) adv[j] = 0;
       if (AFFINE) {
-        const Real c0 = scoef[pl * DIM + 0], c1 = scoef[pl * DIM + 1], c2 = scoef[pl * DIM + 2];
+        const Real c0 = cf[pl * DIM + 0], c1 = cf[pl * DIM + 1], c2 = cf[pl * DIM + 2];
         if (c0 != Real(0)) {
 #pragma unroll
           for (int j = 0; j < n; ++j) {
@@ -218,37 +273,27 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
         if (c1 != Real(0)) {
 #pragma unroll KU
           for (int k = 0; k < n; ++k) {
-            const Real s = c1 * sDi1[k];
             Real w[n];
             load_line<Real, n>(fa + yline(k), TI::sw(k), w);
-#pragma unroll
-            for (int j = 0; j < n; ++j) adv[j] += s * w[j];
+            axpy_line<Real, n>(adv, c1 * sDi1[k], w);
           }
         }
         if (c2 != Real(0)) {
 #pragma unroll KU
           for (int k = 0; k < n; ++k) {
-            const Real s = c2 * sDi2[k];
             Real w[n];
             load_line<Real, n>(fa + zline(k), zswz, w);
-#pragma unroll
-            for (int j = 0; j < n; ++j) adv[j] += s * w[j];
+            axpy_line<Real, n>(adv, c2 * sDi2[k], w);
           }
         }
       } else {
-        // curved elements: adv = sum_l c_l d_l with c_l = sum_k e_k (-B dt dr_l/dx_k) per node
-        int ek[3] = {0, 0, 0};
-        static_for<0, Q>([&](auto ac) {
-          constexpr int aa = decltype(ac)::value;
-          if (aa == a) { ek[0] = V.e[aa][0]; ek[1] = V.e[aa][1]; ek[2] = V.e[aa][2]; }
-        });
+        // curved elements: adv = -B dt sum_l c_l d_l with c_l = sum_k e_k dr_l/dx_k per node
+        const int a = a0 + pl;
+        const Real ek[3] = {mask_sign<Real>(POS[0], NEG[0], a), mask_sign<Real>(POS[1], NEG[1], a),
+                            mask_sign<Real>(POS[2], NEG[2], a)};
         auto coef = [&](int j, int l) -> Real {
-          const Real *gm = sgeo + (L * n + j) * GEO + l * DIM;
-          Real c = 0;
-#pragma unroll
-          for (int k = 0; k < DIM; ++k)
-            if (ek[k] != 0) c += ek[k] > 0 ? gm[k] : -gm[k];
-          return c;
+          const Real *gm = sg + (L * n + j) * 9 + l * DIM;
+          return -Bdt * (ek[0] * gm[0] + ek[1] * gm[1] + ek[2] * gm[2]);
         };
 #pragma unroll
         for (int j = 0; j < n; ++j) {
@@ -263,11 +308,9 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
           for (int j = 0; j < n; ++j) d[j] = 0;
 #pragma unroll KU
           for (int k = 0; k < n; ++k) {
-            const Real s = sDi1[k];
             Real w[n];
             load_line<Real, n>(fa + yline(k), TI::sw(k), w);
-#pragma unroll
-            for (int j = 0; j < n; ++j) d[j] += s * w[j];
+            axpy_line<Real, n>(d, sDi1[k], w);
           }
 #pragma unroll
           for (int j = 0; j < n; ++j) adv[j] += coef(j, 1) * d[j];
@@ -278,74 +321,82 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
           for (int j = 0; j < n; ++j) d[j] = 0;
 #pragma unroll KU
           for (int k = 0; k < n; ++k) {
-            const Real s = sDi2[k];
             Real w[n];
             load_line<Real, n>(fa + zline(k), zswz, w);
-#pragma unroll
-            for (int j = 0; j < n; ++j) d[j] += s * w[j];
+            axpy_line<Real, n>(d, sDi2[k], w);
           }
 #pragma unroll
           for (int j = 0; j < n; ++j) adv[j] += coef(j, 2) * d[j];
         }
       }
-      // element-interior nodes: B f^{s-1} + (-B dt) e.grad f (A f^0 and B dt F* added on output);
-      // element-boundary nodes: weighted share wJ (-B dt) e.grad f for the assembly
+      // element-interior nodes: A f^0 + B f^{s-1} + (-B dt) e.grad f (B dt F* added on
+      // output); element-boundary nodes: weighted share wJ (-B dt) e.grad f
+      Real *ob = so + pl * PS + own;
+      Real f0l[n];
+      if (use_f0) load_line<Real, n>(ob, own_swz, f0l);
+      Real res[n];
 #pragma unroll
       for (int j = 0; j < n; ++j) {
         const bool bnd = edge_line || j == 0 || j == n - 1;
         if (!bnd) {
           res[j] = p.B * v[j] + adv[j];
+          if (use_f0) res[j] += p.A * f0l[j];
         } else {
-          const Real wJ = AFFINE ? Jwl * m.w[j] : sgeo[(L * n + j) * GEO + DIM * DIM];
+          const Real wJ = AFFINE ? Jwl * m.w[j] : swj[L * n + j];
           res[j] = wJ * adv[j];
         }
       }
+      store_line<Real, n>(ob, own_swz, res);
     }
-    __syncthreads();
-    if (active) store_line<Real, n>(sf + pl * PS + own, own_swz, res);
   }
   __syncthreads();
+  if (nw > 0) {
+    // wall terms join the weighted shares of their boundary nodes
+    for (int idx = tid; idx < na * nw; idx += T) {
+      const int k = idx / na, pl = idx - k * na;
+      so[pl * PS + TI::node(p.walls[w0 + k].i)] += wbuf[k * PB + pl];
+    }
+    __syncthreads();
+  }
 
   // ---- outputs, one node per thread with the group's populations (coalesced across the
   //      warp for each population)
   {
-    Real *__restrict__ fout = p.fout;
-    Real *__restrict__ Tr = p.T;
     const size_t EN = (size_t)p.E * p.Nb;
 #pragma unroll
     for (int r = 0; r < NPT; ++r) {
       const int i = tid + r * T;
       if (i < Np) {
-        const int ti = TI::node(i);
+        const Real *sv = so + TI::node(i);
         const int b = p.bslot[i];
         if (b < 0) {
           const int g = l2g[i];
-          const Real rg = p.has_force ? p.rho[g] : Real(0);
-          Real *fo = fout + g;
+          Real *fo = p.fout + (size_t)a0 * G + g;
+          if (p.has_force) {
+            const Real rg = p.rho[g];
 #pragma unroll
-          for (int pl = 0; pl < PB; ++pl) {
-            if (pl < na) {
-              Real out = sf[pl * PS + ti];
-              if (p.stage != 1) out += p.A * sf0[pl * Np + i];
-              if (p.has_force) out += sfc[pl] * rg;
-              fo[(size_t)(a0 + pl) * G] = out;
-            }
+            for (int pl = 0; pl < PB; ++pl)
+              if (pl < na) fo[pl * G] = sv[pl * PS] + fc[pl] * rg;
+          } else if (full) {
+#pragma unroll
+            for (int pl = 0; pl < PB; ++pl) fo[pl * G] = sv[pl * PS];
+          } else {
+#pragma unroll
+            for (int pl = 0; pl < PB; ++pl)
+              if (pl < na) fo[pl * G] = sv[pl * PS];
           }
         } else {
-          Real *tp = Tr + (size_t)e * p.Nb + b;
+          Real *tp = p.T + (size_t)a0 * EN + (size_t)e * p.Nb + b;
+          if (full) {
 #pragma unroll
-          for (int pl = 0; pl < PB; ++pl)
-            if (pl < na) tp[(size_t)(a0 + pl) * EN] = sf[pl * PS + ti];
+            for (int pl = 0; pl < PB; ++pl) tp[pl * EN] = sv[pl * PS];
+          } else {
+#pragma unroll
+            for (int pl = 0; pl < PB; ++pl)
+              if (pl < na) tp[pl * EN] = sv[pl * PS];
+          }
         }
       }
-    }
-  }
-  if (nw > 0) {
-    __syncthreads();
-    const size_t EN = (size_t)p.E * p.Nb;
-    for (int idx = tid; idx < na * nw; idx += T) {
-      const int k = idx / na, pl = idx - k * na;
-      p.T[(size_t)(a0 + pl) * EN + (size_t)e * p.Nb + p.walls[w0 + k].b] += wbuf[k * PB + pl];
     }
   }
 }
