@@ -426,6 +426,20 @@ int build_setup(const selbm_mesh &mesh, int lattice, int N, Setup *S, std::strin
   }
   S->G = G;
 
+  // renumber: element-interior nodes first, element by element in local order (each
+  // element's interior is one contiguous block, written whole by the element kernels),
+  // then element-boundary nodes in order of first appearance (one contiguous range,
+  // written by the assembly)
+  {
+    std::vector<int32_t> nid(G, -1);
+    int32_t next = 0;
+    for (size_t q = 0; q < (size_t)E * Np; ++q)
+      if (S->bslot[q % Np] < 0 && nid[S->l2g[q]] < 0) nid[S->l2g[q]] = next++;
+    for (size_t q = 0; q < (size_t)E * Np; ++q)
+      if (nid[S->l2g[q]] < 0) nid[S->l2g[q]] = next++;
+    for (size_t q = 0; q < (size_t)E * Np; ++q) S->l2g[q] = nid[S->l2g[q]];
+  }
+
   // consistency: interior nodes are unique; boundary nodes only match boundary nodes
   std::vector<int32_t> count(G, 0), nbd(G, 0);
   for (size_t q = 0; q < (size_t)E * Np; ++q) {
