@@ -254,6 +254,23 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
       const int pl = tid / NL + rd * LPR;
       if (pl >= na) break;
       const Real *fa = sf + pl * PS;
+      // t-line k of this task: halves at zlo[k & 3] + k PL and zhi[k & 3] + k PL
+      const Real *zlo[4], *zhi[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        zlo[q] = TI::SW ? fa + zq[q] + zswz : fa;
+        zhi[q] = TI::SW ? fa + zq[q] + (4 ^ zswz) : fa;
+      }
+      auto load_t = [&](int k, Real (&w)[n]) {
+        if constexpr (TI::SW) {
+          const float4 a = *reinterpret_cast<const float4 *>(zlo[k & 3] + k * TI::PL);
+          const float4 b = *reinterpret_cast<const float4 *>(zhi[k & 3] + k * TI::PL);
+          w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+          w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+        } else {
+          load_line<Real, n>(fa + zline(k), zswz, w);
+        }
+      };
       Real v[n];
       load_line<Real, n>(fa + own, own_swz, v);
       Real adv[n];
@@ -271,19 +288,23 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
           }
         }
         if (c1 != Real(0)) {
+          Real dr[n];
+          if (KU == n) load_line<Real, n>(sDi1, 0, dr);
 #pragma unroll KU
           for (int k = 0; k < n; ++k) {
             Real w[n];
             load_line<Real, n>(fa + yline(k), TI::sw(k), w);
-            axpy_line<Real, n>(adv, c1 * sDi1[k], w);
+            axpy_line<Real, n>(adv, c1 * (KU == n ? dr[k] : sDi1[k]), w);
           }
         }
         if (c2 != Real(0)) {
+          Real dr[n];
+          if (KU == n) load_line<Real, n>(sDi2, 0, dr);
 #pragma unroll KU
           for (int k = 0; k < n; ++k) {
             Real w[n];
-            load_line<Real, n>(fa + zline(k), zswz, w);
-            axpy_line<Real, n>(adv, c2 * sDi2[k], w);
+            load_t(k, w);
+            axpy_line<Real, n>(adv, c2 * (KU == n ? dr[k] : sDi2[k]), w);
           }
         }
       } else {
@@ -303,27 +324,29 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
           adv[j] = coef(j, 0) * d;
         }
         {
-          Real d[n];
+          Real d[n], dr[n];
+          if (KU == n) load_line<Real, n>(sDi1, 0, dr);
 #pragma unroll
           for (int j = 0; j < n; ++j) d[j] = 0;
 #pragma unroll KU
           for (int k = 0; k < n; ++k) {
             Real w[n];
             load_line<Real, n>(fa + yline(k), TI::sw(k), w);
-            axpy_line<Real, n>(d, sDi1[k], w);
+            axpy_line<Real, n>(d, KU == n ? dr[k] : sDi1[k], w);
           }
 #pragma unroll
           for (int j = 0; j < n; ++j) adv[j] += coef(j, 1) * d[j];
         }
         {
-          Real d[n];
+          Real d[n], dr[n];
+          if (KU == n) load_line<Real, n>(sDi2, 0, dr);
 #pragma unroll
           for (int j = 0; j < n; ++j) d[j] = 0;
 #pragma unroll KU
           for (int k = 0; k < n; ++k) {
             Real w[n];
-            load_line<Real, n>(fa + zline(k), zswz, w);
-            axpy_line<Real, n>(d, sDi2[k], w);
+            load_t(k, w);
+            axpy_line<Real, n>(d, KU == n ? dr[k] : sDi2[k], w);
           }
 #pragma unroll
           for (int j = 0; j < n; ++j) adv[j] += coef(j, 2) * d[j];
@@ -332,18 +355,22 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
       // element-interior nodes: A f^0 + B f^{s-1} + (-B dt) e.grad f (B dt F* added on
       // output); element-boundary nodes: weighted share wJ (-B dt) e.grad f
       Real *ob = so + pl * PS + own;
-      Real f0l[n];
-      if (use_f0) load_line<Real, n>(ob, own_swz, f0l);
+      auto wJ = [&](int j) -> Real { return AFFINE ? Jwl * m.w[j] : swj[L * n + j]; };
       Real res[n];
+      if (edge_line) {
 #pragma unroll
-      for (int j = 0; j < n; ++j) {
-        const bool bnd = edge_line || j == 0 || j == n - 1;
-        if (!bnd) {
-          res[j] = p.B * v[j] + adv[j];
-          if (use_f0) res[j] += p.A * f0l[j];
+        for (int j = 0; j < n; ++j) res[j] = wJ(j) * adv[j];
+      } else {
+        res[0] = wJ(0) * adv[0];
+        res[n - 1] = wJ(n - 1) * adv[n - 1];
+        if (use_f0) {
+          Real f0l[n];
+          load_line<Real, n>(ob, own_swz, f0l);
+#pragma unroll
+          for (int j = 1; j < n - 1; ++j) res[j] = p.B * v[j] + adv[j] + p.A * f0l[j];
         } else {
-          const Real wJ = AFFINE ? Jwl * m.w[j] : swj[L * n + j];
-          res[j] = wJ * adv[j];
+#pragma unroll
+          for (int j = 1; j < n - 1; ++j) res[j] = p.B * v[j] + adv[j];
         }
       }
       store_line<Real, n>(ob, own_swz, res);
