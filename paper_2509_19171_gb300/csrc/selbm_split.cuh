@@ -533,7 +533,7 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
   Real *so = h2 + H;                                // [2]
   Real *spart = so + 2;                             // [NW][2n]
   __shared__ double dred[NW][2];
-  __shared__ int s_r, in_range;
+  __shared__ int s_r, in_range, s_mode[n];
   const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int32_t *l2g = p.l2g + (size_t)e * Np;
   const size_t G = p.G;
@@ -552,39 +552,43 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
     for (int k = tid; k < n * n; k += T) { sM1[k] = c.Vinv[k]; sVm[k] = c.Vm[k]; }
     if (tid == 0) in_range = 1;
   }
-  // ---- gather; the learned control also takes rho - rho0 and |u| at every node
-  double pm = 0.0, pk = 0.0;
+  // ---- gather with asynchronous copies (all Q populations of the thread's nodes in
+  //      flight at once); the learned control then takes rho - rho0 and |u| at every node
   {
-    const Real *__restrict__ fin = p.fin;
+    const unsigned s_f = (unsigned)__cvta_generic_to_shared(sf);
     for (int i = tid; i < Np; i += T) {
-      const size_t g = l2g[i];
+      const Real *src = p.fin + l2g[i];
+      const unsigned d = s_f + (unsigned)TI::node(i) * (unsigned)sizeof(Real);
+#pragma unroll
+      for (int a = 0; a < Q; ++a) cp_async_s<Real>(d + a * PS * (unsigned)sizeof(Real), src + a * G);
+    }
+    cp_async_wait_all();
+  }
+  double pm = 0.0, pk = 0.0;
+  if (LEARNED) {
+    for (int i = tid; i < Np; i += T) {        // the nodes this thread copied
       const int ti = TI::node(i);
       Real drho = 0, j[3] = {0, 0, 0};
       static_for<0, Q>([&](auto ac) {
         constexpr int a = decltype(ac)::value;
-        const Real v = fin[(size_t)a * G + g];
-        sf[a * PS + ti] = v;
-        if (LEARNED) {
-          drho += v;
+        const Real v = sf[a * PS + ti];
+        drho += v;
 #pragma unroll
-          for (int k = 0; k < DIM; ++k) {
-            if (V.e[a][k] > 0) j[k] += v;
-            else if (V.e[a][k] < 0) j[k] -= v;
-          }
+        for (int k = 0; k < DIM; ++k) {
+          if (V.e[a][k] > 0) j[k] += v;
+          else if (V.e[a][k] < 0) j[k] -= v;
         }
       });
-      if (LEARNED) {
-        const Real rho = p.rho0 + drho;
-        Real uu = 0;
+      const Real rho = p.rho0 + drho;
+      Real uu = 0;
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) uu += (j[k] / rho) * (j[k] / rho);
-        sq[ti] = drho;
-        sq[PS + ti] = sqrt(uu);
-        if (c.acc) {
-          const double wq = (double)weight(i);
-          pm += wq * (double)rho;
-          pk += 0.5 * (double)p.rho0 * wq * (double)uu;
-        }
+      for (int k = 0; k < DIM; ++k) uu += (j[k] / rho) * (j[k] / rho);
+      sq[ti] = drho;
+      sq[PS + ti] = sqrt(uu);
+      if (c.acc) {
+        const double wq = (double)weight(i);
+        pm += wq * (double)rho;
+        pk += 0.5 * (double)p.rho0 * wq * (double)uu;
       }
     }
   }
@@ -680,17 +684,41 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
     }
     if (!c.outputs) return;
     __syncthreads();
-    // F_e = V diag(sigma) V^-1 with exact identity end rows
-    for (int k = tid; k < n * n; k += T) {
-      const int r = k / n, jj = k - r * n;
-      Real s = 0;
-#pragma unroll
-      for (int q = 0; q < n; ++q) s += sVm[r * n + q] * ssig[q] * sM1[q * n + jj];
-      if (r == 0 || r == n - 1) s = (r == jj) ? Real(1) : Real(0);
-      sM0[k] = s;
+    // F_e = V diag(sigma) V^-1 with exact identity end rows, = I + U W with U = V[:, d]
+    // diag(sigma_d - 1) (end rows zero) and W = V^-1[d, :] over the damped modes d: the
+    // low-rank form when it is cheaper (2 r n < n^2 multiply-adds per line)
+    if (tid == 0) {
+      int r = 0;
+      for (int k = 0; k < n; ++k)
+        if (ssig[k] != Real(1)) s_mode[r++] = k;
+      s_r = r;
     }
     __syncthreads();
-    tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { dense_vals<Real, n>(v, sM0); });
+    const int r = s_r;
+    Real *sW = sq;                                     // the modal fields are no longer needed
+    if (2 * r < n) {
+      for (int idx = tid; idx < n * r; idx += T) {
+        const int j = idx / r, q = idx - j * r, k = s_mode[q];
+        sM0[j * n + q] = (j == 0 || j == n - 1) ? Real(0) : sVm[j * n + k] * (ssig[k] - Real(1));
+      }
+      for (int idx = tid; idx < r * n; idx += T) {
+        const int q = idx / n, jj = idx - q * n;
+        sW[q * n + jj] = sM1[s_mode[q] * n + jj];
+      }
+      __syncthreads();
+      tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { filter_vals<Real, n>(v, sM0, sW, r); });
+    } else {
+      for (int k = tid; k < n * n; k += T) {
+        const int rr = k / n, jj = k - rr * n;
+        Real s = 0;
+#pragma unroll
+        for (int q = 0; q < n; ++q) s += sVm[rr * n + q] * ssig[q] * sM1[q * n + jj];
+        if (rr == 0 || rr == n - 1) s = (rr == jj) ? Real(1) : Real(0);
+        sM0[k] = s;
+      }
+      __syncthreads();
+      tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { dense_vals<Real, n>(v, sM0); });
+    }
   } else if (MODE == PRO_FIXED) {
     const int r = s_r;
     tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { filter_vals<Real, n>(v, sM0, sM1, r); });
