@@ -45,6 +45,24 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
 
 
+def measured_traffic(kernel_key, units):
+    """DRAM bytes (read + write) per launch of `kernel_key` from the committed ncu summary
+    (profiles/traffic.json: bytes per element measured on a smaller mesh, scaled by the
+    elements one launch processes); None when the kernel source has changed since."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh).get(kernel_key)
+    if not d:
+        return None
+    src = os.path.join(ROOT, d["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != d["source_sha256"]:
+        return None
+    return d["dram_bytes_per_element"] * units
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -135,7 +153,7 @@ class ClockSampler:
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                                          "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -284,7 +302,7 @@ def workload_config(case, form, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "pipe", "shear"])
@@ -425,7 +443,9 @@ def main():
         achieved = r["stage23_bytes"] / (r["stage23_ms"] * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "peak_source": f"{pk_kind} hbm_gbs (of {pk_kind})",
-                "bytes_per_launch": r["stage23_bytes"], "traffic": None}
+                "bytes_per_launch": r["stage23_bytes"],
+                "traffic": measured_traffic("stage_split_float_d3q27_n8_stage23" if r["step_form"] == "population-split"
+                                            else None, case.mesh.nelem)}
 
     line = {"metric": metric, "value": r["value"], "unit": "node-pop updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],

@@ -98,7 +98,7 @@ __device__ __forceinline__ void cp_async_s(unsigned dst, const Real *src) {
 // one Runge-Kutta stage for PB populations of one element
 // ---------------------------------------------------------------------------
 template <typename Real, int LAT, int n, bool AFFINE>
-__global__ void __launch_bounds__(SplitShape<LAT, n>::THREADS, (sizeof(Real) == 4 ? 4 : 2))
+__global__ void __launch_bounds__(SplitShape<LAT, n>::THREADS, (sizeof(Real) == 4 ? (AFFINE ? 5 : 4) : 2))
 stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   using S = SplitShape<LAT, n>;
   constexpr int Q = S::Q, DIM = 3, Np = S::Np, NL = S::NL, T = S::THREADS, PB = S::PB, NG = S::NG;
@@ -232,6 +232,102 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   // ---- (population, r-line) tasks, ROUNDS per thread with the same r-line (i1, i2);
   //      a task reads f^{s-1} lines from sf and replaces its own line of so (f^0 in,
   //      result out), which no other task touches
+  if constexpr (AFFINE && TI::SW) {
+    // swizzled FP32 tile (N = 7): one warp per population, each thread two r-lines
+    // (i1, i2) and (i1, i2 + 4) that share their t-lines, so every t-line read from
+    // shared memory serves both; the s-lines of line B sit 4 planes below those of A
+    const int pl = tid >> 5, lane = tid & 31;
+    const int i1 = lane & 7, i2 = lane >> 3;                 // i2 in 0..3
+    if (pl < na) {
+      const Real *fa = sf + pl * PS;
+      const Real c0 = cf[pl * DIM + 0], c1 = cf[pl * DIM + 1], c2 = cf[pl * DIM + 2];
+      const int ownA = TI::line(i1, i2), swz = TI::sw(i1);   // line B = ownA + 4 PL, same swizzle
+      Real accA[n], accB[n];
+#pragma unroll
+      for (int j = 0; j < n; ++j) { accA[j] = 0; accB[j] = 0; }
+      if (c0 != Real(0)) {
+        Real v[n];
+        load_line<Real, n>(fa + ownA, swz, v);
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          Real d = 0;
+#pragma unroll
+          for (int k = 0; k < n; ++k) d += m.D[j * n + k] * v[k];
+          accA[j] = c0 * d;
+        }
+        load_line<Real, n>(fa + ownA + 4 * TI::PL, swz, v);
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          Real d = 0;
+#pragma unroll
+          for (int k = 0; k < n; ++k) d += m.D[j * n + k] * v[k];
+          accB[j] = c0 * d;
+        }
+      }
+      if (c1 != Real(0)) {
+        // s-lines (k, i2) and (k, i2 + 4); coefficient c1 D[i1][k] for both
+        Real dr[n];
+        load_line<Real, n>(sD + i1 * n, 0, dr);
+        const Real *ya[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ya[q] = fa + i2 * TI::PL + ((q ^ i2) << 3);
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+          const Real sk = c1 * dr[k];
+          const Real *la = ya[k & 3] + ((k & 4) << 3);
+          Real w[n];
+          load_line<Real, n>(la, TI::sw(k), w);
+          axpy_line<Real, n>(accA, sk, w);
+          load_line<Real, n>(la + 4 * TI::PL, TI::sw(k), w);
+          axpy_line<Real, n>(accB, sk, w);
+        }
+      }
+      if (c2 != Real(0)) {
+        // t-lines (i1, k): coefficients c2 D[i2][k] (line A) and c2 D[i2 + 4][k] (line B)
+        Real da[n], db[n];
+        load_line<Real, n>(sD + i2 * n, 0, da);
+        load_line<Real, n>(sD + (i2 + 4) * n, 0, db);
+        const Real *zb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) zb[q] = fa + ((i1 ^ q) << 3);
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+          Real w[n];
+          load_line<Real, n>(zb[k & 3] + k * TI::PL, swz, w);
+          axpy_line<Real, n>(accA, c2 * da[k], w);
+          axpy_line<Real, n>(accB, c2 * db[k], w);
+        }
+      }
+      // stage combination of both lines, in place of their f^0
+      const Real Jw1 = p.el_J[e] * sw[i1];
+      auto finish = [&](Real (&acc)[n], int own, bool edge, Real Jwl) {
+        Real *ob = so + pl * PS + own;
+        Real res[n];
+        if (edge) {
+#pragma unroll
+          for (int j = 0; j < n; ++j) res[j] = Jwl * m.w[j] * acc[j];
+        } else {
+          Real v[n];
+          load_line<Real, n>(fa + own, swz, v);
+          res[0] = Jwl * m.w[0] * acc[0];
+          res[n - 1] = Jwl * m.w[n - 1] * acc[n - 1];
+          if (use_f0) {
+            Real f0l[n];
+            load_line<Real, n>(ob, swz, f0l);
+#pragma unroll
+            for (int j = 1; j < n - 1; ++j) res[j] = p.B * v[j] + acc[j] + p.A * f0l[j];
+          } else {
+#pragma unroll
+            for (int j = 1; j < n - 1; ++j) res[j] = p.B * v[j] + acc[j];
+          }
+        }
+        store_line<Real, n>(ob, swz, res);
+      };
+      const bool edge1 = i1 == 0 || i1 == n - 1;
+      finish(accA, ownA, edge1 || i2 == 0, Jw1 * sw[i2]);
+      finish(accB, ownA + 4 * TI::PL, edge1 || i2 + 4 == n - 1, Jw1 * sw[i2 + 4]);
+    }
+  } else
   {
     const int L = tid % NL;
     const int i1 = L % n, i2 = L / n;
@@ -498,6 +594,27 @@ __device__ __forceinline__ void tile_pass3(Real *sf, int tid, Op op) {
   __syncthreads();
 }
 
+// v <- v + U (W v) with U^T and W stored by rows in shared memory (row stride n), the
+// rows read as vectors
+template <typename Real, int n>
+__device__ __forceinline__ void filter_rows(Real (&v)[n], const Real *UT, const Real *W, int r) {
+  Real o[n];
+#pragma unroll
+  for (int j = 0; j < n; ++j) o[j] = v[j];
+  for (int q = 0; q < r; ++q) {
+    Real row[n];
+    load_line<Real, n>(W + q * n, 0, row);
+    Real s = 0;
+#pragma unroll
+    for (int k = 0; k < n; ++k) s += row[k] * v[k];
+    load_line<Real, n>(UT + q * n, 0, row);
+#pragma unroll
+    for (int j = 0; j < n; ++j) o[j] += row[j] * s;
+  }
+#pragma unroll
+  for (int j = 0; j < n; ++j) v[j] = o[j];
+}
+
 template <typename Real, int n>
 __device__ __forceinline__ void dense_vals(Real (&v)[n], const Real *M) {
   Real o[n];
@@ -513,7 +630,7 @@ __device__ __forceinline__ void dense_vals(Real (&v)[n], const Real *M) {
 }
 
 template <typename Real, int LAT, int n, bool AFFINE, int MODE>
-__global__ void __launch_bounds__(kProThreads)
+__global__ void __launch_bounds__(kProThreads, sizeof(Real) == 4 ? (MODE == PRO_LEARNED ? 3 : 4) : 1)
 prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedIn<Real, n> c) {
   constexpr int Q = LT<LAT>::v.Q, DIM = 3, Np = n * n * n, T = kProThreads, NW = T / 32, H = kHidden, nin = 2 * n;
   using TI = Tile<Real, n, DIM>;
@@ -522,8 +639,8 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
   constexpr bool LEARNED = MODE == PRO_LEARNED;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real *sf = reinterpret_cast<Real *>(smem_raw);   // [Q][PS]
-  Real *sM0 = sf + Q * PS;                          // [n][n] U (fixed) or F_e (learned)
-  Real *sM1 = sM0 + n * n;                          // [n][n] W (fixed) or V^-1 (learned)
+  Real *sM0 = sf + Q * PS;                          // learned: [n][n] F_e or U_e^T
+  Real *sM1 = sM0 + n * n;                          // learned: [n][n] V^-1
   Real *sq = sM1 + n * n;                           // learned: [2][PS] rho - rho0, |u| -> modal
   Real *sVm = sq + 2 * PS;                          // [n][n]
   Real *ssig = sVm + n * n;                         // [n]
@@ -544,10 +661,6 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
     }
     return p.wJ[(size_t)e * Np + i];
   };
-  if (MODE == PRO_FIXED) {
-    for (int k = tid; k < n * n; k += T) { sM0[k] = m.U[k]; sM1[k] = m.W[k]; }
-    if (tid == 0) s_r = m.r;
-  }
   if (LEARNED) {
     for (int k = tid; k < n * n; k += T) { sM1[k] = c.Vinv[k]; sVm[k] = c.Vm[k]; }
     if (tid == 0) in_range = 1;
@@ -697,16 +810,16 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
     const int r = s_r;
     Real *sW = sq;                                     // the modal fields are no longer needed
     if (2 * r < n) {
-      for (int idx = tid; idx < n * r; idx += T) {
-        const int j = idx / r, q = idx - j * r, k = s_mode[q];
-        sM0[j * n + q] = (j == 0 || j == n - 1) ? Real(0) : sVm[j * n + k] * (ssig[k] - Real(1));
+      for (int idx = tid; idx < n * r; idx += T) {       // U^T [q][j]
+        const int q = idx / n, j = idx - q * n, k = s_mode[q];
+        sM0[q * n + j] = (j == 0 || j == n - 1) ? Real(0) : sVm[j * n + k] * (ssig[k] - Real(1));
       }
-      for (int idx = tid; idx < r * n; idx += T) {
+      for (int idx = tid; idx < r * n; idx += T) {       // W [q][k]
         const int q = idx / n, jj = idx - q * n;
         sW[q * n + jj] = sM1[s_mode[q] * n + jj];
       }
       __syncthreads();
-      tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { filter_vals<Real, n>(v, sM0, sW, r); });
+      tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { filter_rows<Real, n>(v, sM0, sW, r); });
     } else {
       for (int k = tid; k < n * n; k += T) {
         const int rr = k / n, jj = k - rr * n;
@@ -720,8 +833,9 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
       tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { dense_vals<Real, n>(v, sM0); });
     }
   } else if (MODE == PRO_FIXED) {
-    const int r = s_r;
-    tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { filter_vals<Real, n>(v, sM0, sM1, r); });
+    // U and W are the same for every element: read them as kernel-parameter constants
+    const int r = m.r;
+    tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { filter_vals<Real, n>(v, m.U, m.W, r); });
   }
 
   // ---- collision at every node this element writes: owned copies (one filter for
