@@ -92,13 +92,15 @@ def test_split_unfiltered_closed_box(P, monkeypatch):
         assert rel(s.get_state(), o.to_local(f)) <= 1e-12, k
 
 
-def test_split_fp32_default_and_accuracy(P):
-    """FP32 hexahedral handles take the split form by default; one step within 1e-6."""
+@pytest.mark.parametrize("lat,N", [("D3Q27", 7), ("D3Q27", 5), ("D3Q19", 7), ("D3Q19", 4)])
+def test_split_fp32_default_and_accuracy(P, lat, N):
+    """FP32 hexahedral handles take the split form by default at every compiled order; each
+    step within 1e-6 of the FP64 oracle."""
     L = 2 * math.pi
     mesh = W.box_mesh((2, 2, 2), (0, 0, 0), (L, L, L), (True, True, True))
-    filt = {"shape": 0, "gamma": 0.1, "kc": 5.0}
-    o = OracleSELBM(mesh, "D3Q27", 7, 1e-3, filt=filt)
-    s = P.SELBM(mesh, "D3Q27", 7, 1e-3, precision=P.FP32DEV, filt=filt)
+    filt = {"shape": 0, "gamma": 0.1, "kc": float(N - 2)}
+    o = OracleSELBM(mesh, lat, N, 1e-3, filt=filt)
+    s = P.SELBM(mesh, lat, N, 1e-3, precision=P.FP32DEV, filt=filt)
     assert s.split
     f = random_continuous_state(o, 0.03, 8)
     s.set_state(np.ascontiguousarray(o.to_local(f)))
@@ -176,6 +178,23 @@ def test_split_fp32_walls_every_face(P):
     f = random_continuous_state(o, 0.01, 5)
     s.set_state(np.ascontiguousarray(o.to_local(f)))
     for _ in range(3):
+        f = o.step(f)
+        s.step(1)
+        assert rel(s.get_state(), o.to_local(f)) <= 1e-6
+
+
+def test_split_fp32_curved_pipe(P):
+    """FP32 curved elements (per-node metrics), flux bounce-back and body force in the
+    split form, D3Q19 N = 4, within 1e-6 of the FP64 oracle over two steps."""
+    mesh = W.pipe_mesh(n_core=2, n_radial=2, n_axial=2, length=1.0)
+    filt = {"shape": 0, "gamma": 0.1, "kc": 2.0}
+    g = (0.0, 0.0, 2e-4)
+    o = OracleSELBM(mesh, "D3Q19", 4, 2e-3, filt=filt, body_accel=g)
+    s = P.SELBM(mesh, "D3Q19", 4, 2e-3, precision=P.FP32DEV, filt=filt, body_accel=g)
+    assert s.split
+    f = random_continuous_state(o, 0.02, 9)
+    s.set_state(np.ascontiguousarray(o.to_local(f)))
+    for _ in range(2):
         f = o.step(f)
         s.step(1)
         assert rel(s.get_state(), o.to_local(f)) <= 1e-6
