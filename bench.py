@@ -438,14 +438,16 @@ def main():
                 "traffic": None}
     else:
         # dominant kernel: the stage 2/3 kernel (two launches per step)
-        name = ("stage_split_kernel<float, D3Q27, N=7> (stages 2, 3)" if r["step_form"] == "population-split"
-                else "stage_fast_kernel<float, D3Q27, N=7> (stages 2, 3)")
+        geom = "affine" if info["affine"] else "curved"
+        kern = "stage_split_kernel" if r["step_form"] == "population-split" else "stage_fast_kernel"
+        name = f"{kern}<float, {case.lattice}, N={case.order}, {geom}> (stages 2, 3)"
+        # ncu traffic only for the kernel instantiation it was captured on
+        tkey = f"{kern}_float_{case.lattice.lower()}_n{case.order + 1}_{geom}_stage23"
         achieved = r["stage23_bytes"] / (r["stage23_ms"] * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "peak_source": f"{pk_kind} hbm_gbs (of {pk_kind})",
                 "bytes_per_launch": r["stage23_bytes"],
-                "traffic": measured_traffic("stage_split_float_d3q27_n8_stage23" if r["step_form"] == "population-split"
-                                            else None, case.mesh.nelem)}
+                "traffic": measured_traffic(tkey, case.mesh.nelem)}
 
     line = {"metric": metric, "value": r["value"], "unit": "node-pop updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
