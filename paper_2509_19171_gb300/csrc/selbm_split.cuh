@@ -557,8 +557,9 @@ constexpr size_t prologue_smem_bytes() {
 }
 
 // y <- (A x A x A) y on NP populations of a tile, one 1D pass per axis; op maps the n
-// values of one line in place
-template <typename Real, int n, int NP, int T, typename Op>
+// values of one line in place.  PAIRS: on the swizzled FP32 tile, the s- and t-passes take
+// two adjacent columns per task with 8-byte accesses (for light ops; heavy ops spill)
+template <typename Real, int n, int NP, int T, bool PAIRS = false, typename Op>
 __device__ __forceinline__ void tile_pass3(Real *sf, int tid, Op op) {
   using TI = Tile<Real, n, 3>;
   constexpr int NL = n * n, PS = TI::PS;
@@ -572,26 +573,62 @@ __device__ __forceinline__ void tile_pass3(Real *sf, int tid, Op op) {
     store_line<Real, n>(base, TI::sw(i1), v);
   }
   __syncthreads();
-  for (int t = tid; t < NP * NL; t += T) {          // s-lines
-    const int a = t / NL, r = t - a * NL, i0 = r % n, i2 = r / n;
-    Real v[n];
+  if constexpr (TI::SW && PAIRS) {
+    // swizzled FP32 tile: two adjacent columns per task (i0 = 2q, 2q + 1 sit in one aligned
+    // 8-byte pair of every line), one vector access per line
+    auto pair_pass = [&](auto addr) {
+      for (int t = tid; t < NP * NL / 2; t += T) {
+        const int a = t / (NL / 2), r = t - a * (NL / 2), q = r & 3, w = r >> 2;
+        float2 v2[n];
 #pragma unroll
-    for (int k = 0; k < n; ++k) v[k] = sf[a * PS + TI::at(i0, k, i2)];
-    op(v);
+        for (int k = 0; k < n; ++k) v2[k] = *reinterpret_cast<const float2 *>(sf + a * PS + addr(w, k, q));
+        {
+          Real v[n];
 #pragma unroll
-    for (int k = 0; k < n; ++k) sf[a * PS + TI::at(i0, k, i2)] = v[k];
+          for (int k = 0; k < n; ++k) v[k] = v2[k].x;
+          op(v);
+#pragma unroll
+          for (int k = 0; k < n; ++k) v2[k].x = v[k];
+        }
+        {
+          Real v[n];
+#pragma unroll
+          for (int k = 0; k < n; ++k) v[k] = v2[k].y;
+          op(v);
+#pragma unroll
+          for (int k = 0; k < n; ++k) v2[k].y = v[k];
+        }
+#pragma unroll
+        for (int k = 0; k < n; ++k) *reinterpret_cast<float2 *>(sf + a * PS + addr(w, k, q)) = v2[k];
+      }
+    };
+    // s-lines (i0 pair, k, i2 = w) and t-lines (i0 pair, i1 = w, k)
+    pair_pass([](int w, int k, int q) { return TI::line(k, w) + ((2 * q) ^ TI::sw(k)); });
+    __syncthreads();
+    pair_pass([](int w, int k, int q) { return TI::line(w, k) + ((2 * q) ^ TI::sw(w)); });
+    __syncthreads();
+  } else {
+    for (int t = tid; t < NP * NL; t += T) {          // s-lines
+      const int a = t / NL, r = t - a * NL, i0 = r % n, i2 = r / n;
+      Real v[n];
+#pragma unroll
+      for (int k = 0; k < n; ++k) v[k] = sf[a * PS + TI::at(i0, k, i2)];
+      op(v);
+#pragma unroll
+      for (int k = 0; k < n; ++k) sf[a * PS + TI::at(i0, k, i2)] = v[k];
+    }
+    __syncthreads();
+    for (int t = tid; t < NP * NL; t += T) {          // t-lines
+      const int a = t / NL, r = t - a * NL, i0 = r % n, i1 = r / n;
+      Real v[n];
+#pragma unroll
+      for (int k = 0; k < n; ++k) v[k] = sf[a * PS + TI::at(i0, i1, k)];
+      op(v);
+#pragma unroll
+      for (int k = 0; k < n; ++k) sf[a * PS + TI::at(i0, i1, k)] = v[k];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int t = tid; t < NP * NL; t += T) {          // t-lines
-    const int a = t / NL, r = t - a * NL, i0 = r % n, i1 = r / n;
-    Real v[n];
-#pragma unroll
-    for (int k = 0; k < n; ++k) v[k] = sf[a * PS + TI::at(i0, i1, k)];
-    op(v);
-#pragma unroll
-    for (int k = 0; k < n; ++k) sf[a * PS + TI::at(i0, i1, k)] = v[k];
-  }
-  __syncthreads();
 }
 
 // v <- v + U (W v) with U^T and W stored by rows in shared memory (row stride n), the
@@ -835,7 +872,7 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
   } else if (MODE == PRO_FIXED) {
     // U and W are the same for every element: read them as kernel-parameter constants
     const int r = m.r;
-    tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { filter_vals<Real, n>(v, m.U, m.W, r); });
+    tile_pass3<Real, n, Q, T, true>(sf, tid, [&](Real (&v)[n]) { filter_vals<Real, n>(v, m.U, m.W, r); });
   }
 
   // ---- collision at every node this element writes: owned copies (one filter for
