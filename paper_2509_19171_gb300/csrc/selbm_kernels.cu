@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(512) stage_kernel(const KParams<Real> p) {
 // where T_c = B dt x (weighted contribution of copy c); copies summed in ascending (element, local node) order
 // ---------------------------------------------------------------------------
 template <typename Real, int LAT>
-__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 1) dss_kernel(const KParams<Real> p) {
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) dss_kernel(const KParams<Real> p) {
   constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
   const Real Bdt = p.B * p.dt;
   const size_t EN = (size_t)p.E * p.Nb;
