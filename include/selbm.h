@@ -164,6 +164,29 @@ int selbm_set_body_force(selbm_t *h, const double g[3]);
  * Returns SELBM_ERR_NONFINITE if the state holds NaN/Inf.
  */
 int selbm_diagnostics(selbm_t *h, double out[8]);
+/*
+ * Pipe-flow statistics (Sec. 4, turbulent pipe: tau_w evaluated at the boundary nodes,
+ * mean axial velocity averaged in space and time), of the current (filtered) state.
+ *
+ * selbm_wall_stress: wall shear stress along the direction dir (normalised here), the
+ * average over every wall face, weighted by the surface quadrature weights w_s J_s, of
+ * -mu n . grad(u . dir) at the face's GLL nodes; n is the outward unit normal, the
+ * gradient is the element's GLL derivative with the chain rule, mu = rho0 nu.  A node on
+ * several wall faces contributes once per face.  *tau = 0 on meshes without walls.
+ * For the pipe, tau_w of the paper (mu (sin theta du_z/dy + cos theta du_z/dx)) with
+ * dir = the axis.  Errors: SELBM_ERR_ARG (NULL or zero dir), SELBM_ERR_STATE, SELBM_ERR_CUDA.
+ *
+ * selbm_radial_profile: unique nodes binned by their distance r from the line through
+ * origin along axis, bin = min(floor(r nbins / radius), nbins - 1); mean[b] = sum M_g
+ * (u_g . axis) / mass[b], mass[b] = sum M_g (lumped mass), host buffers of nbins
+ * values (mean[b] = 0 for an empty bin).  Time averages are the caller's: average the
+ * mean profiles of successive calls weighted by mass.  1 <= nbins <=
+ * SELBM_PROFILE_MAX_BINS.  Errors as selbm_wall_stress.
+ */
+#define SELBM_PROFILE_MAX_BINS 2048
+int selbm_wall_stress(selbm_t *h, const double dir[3], double *tau);
+int selbm_radial_profile(selbm_t *h, const double origin[3], const double axis[3], double radius, int nbins,
+                         double *mean, double *mass);
 
 /* ------------------------------------------------------------------------
  * Learned per-element filter control.  Not in the paper, whose fixed explicit

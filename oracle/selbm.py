@@ -235,6 +235,42 @@ class OracleSELBM:
         dens = 2 * mu * diag - 2.0 / 3.0 * mu * div ** 2 + mu * off
         return float((self.wJ * dens).sum())
 
+    def wall_stress(self, f, direction):
+        """Wall shear stress along `direction` (Sec. 4, pipe flow: tau_w from the boundary nodes,
+        tau_w = mu (sin theta du_z/dy + cos theta du_z/dx) on the pipe wall): the average over every
+        wall face, weighted by w_s J_s, of -mu n . grad(u . d) at the face's GLL nodes, n the
+        outward unit normal, mu = rho0 nu, gradients by D along each reference axis and the chain
+        rule (as in `dissipation`)."""
+        _, u = self.moments(f)
+        d = np.asarray(direction, float)[: self.dim]
+        d = d / np.linalg.norm(d)
+        ud = (u @ d)[self.glo]                                                        # [E, Np]
+        dr = np.stack([geo.apply_axis(self.D, ud, l, self.N, self.dim) for l in range(self.dim)], -1)
+        grad = np.einsum("eplk,epl->epk", self.drdx, dr)                             # d(u.d)/dx_k
+        mu = self.rho0 * self.nu
+        num = den = 0.0
+        for (el, nodes, n, wsJs, wid) in self.walls:
+            dn = (n * grad[el, nodes]).sum(1)
+            num += float((wsJs * (-mu * dn)).sum())
+            den += float(wsJs.sum())
+        return num / den if den > 0 else 0.0
+
+    def radial_profile(self, f, origin, axis, radius, nbins):
+        """Mean of u . axis over unique nodes binned by their distance r from the line through
+        `origin` along `axis` (Sec. 4: space-averaged axial velocity): bin = min(floor(r nbins /
+        radius), nbins - 1), weights = lumped mass M_g.  Returns (mean per bin, mass per bin)."""
+        _, u = self.moments(f)
+        a = np.asarray(axis, float)[: self.dim]
+        a = a / np.linalg.norm(a)
+        x = self.Xg - np.asarray(origin, float)[: self.dim]
+        y = x - np.outer(x @ a, a)
+        r = np.sqrt((y * y).sum(1))
+        b = np.minimum(np.floor(r * nbins / radius).astype(int), nbins - 1)
+        mass = np.bincount(b, weights=self.mass, minlength=nbins)
+        su = np.bincount(b, weights=self.mass * (u @ a), minlength=nbins)
+        mean = np.divide(su, mass, out=np.zeros(nbins), where=mass > 0)
+        return mean, mass
+
     def integrals(self, f):
         """Quadrature integrals: mass sum M rho, momentum sum M rho u, KE = sum M rho0 |u|^2 / 2."""
         rho, u = self.moments(f)

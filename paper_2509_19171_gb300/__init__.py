@@ -27,6 +27,7 @@ ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_MESH", -3: "ERR_CUDA", -4: "ERR_NONFI
 EXPORTS = ["selbm_create", "selbm_destroy", "selbm_last_error", "selbm_info", "selbm_lattice_table",
            "selbm_node_coords", "selbm_init", "selbm_set_state", "selbm_get_state", "selbm_step",
            "selbm_moments", "selbm_set_filter", "selbm_set_body_force", "selbm_diagnostics", "selbm_sync",
+           "selbm_wall_stress", "selbm_radial_profile",
            "selbm_mesh_check", "selbm_timers", "selbm_timers_read", "selbm_set_learned_filter",
            "selbm_clear_learned_filter", "selbm_learned_status", "selbm_element_sigma", "selbm_features",
            "selbm_element_errors", "selbm_mlp_nparams", "selbm_mlp_grad", "selbm_mlp_forward", "selbm_mlp_train"]
@@ -83,6 +84,8 @@ def load_library(path: str = LIB_PATH):
     lib.selbm_set_filter.argtypes = [P, C.POINTER(FilterC)]
     lib.selbm_set_body_force.argtypes = [P, D]
     lib.selbm_diagnostics.argtypes = [P, D]
+    lib.selbm_wall_stress.argtypes = [P, D, D]
+    lib.selbm_radial_profile.argtypes = [P, D, D, C.c_double, I, D, D]
     lib.selbm_sync.argtypes = [P]
     F = C.POINTER(C.c_float)
     lib.selbm_set_learned_filter.argtypes = [P, F, F, F, C.c_double, C.c_double]
@@ -272,6 +275,22 @@ class SELBM:
         out = np.zeros(8)
         self._check(self.lib.selbm_diagnostics(self.h, _dptr(out)))
         return out
+
+    def wall_stress(self, direction):
+        """Surface-weighted mean wall shear stress along `direction` (selbm_wall_stress)."""
+        d = np.ascontiguousarray(np.resize(np.asarray(direction, np.float64), 3))
+        out = np.zeros(1)
+        self._check(self.lib.selbm_wall_stress(self.h, _dptr(d), _dptr(out)))
+        return float(out[0])
+
+    def radial_profile(self, origin, axis, radius, nbins):
+        """(mean of u.axis, lumped mass) per radial bin (selbm_radial_profile)."""
+        o = np.ascontiguousarray(np.resize(np.asarray(origin, np.float64), 3))
+        a = np.ascontiguousarray(np.resize(np.asarray(axis, np.float64), 3))
+        mean, mass = np.zeros(nbins), np.zeros(nbins)
+        self._check(self.lib.selbm_radial_profile(self.h, _dptr(o), _dptr(a), float(radius), int(nbins),
+                                                  _dptr(mean), _dptr(mass)))
+        return mean, mass
 
     def timers(self, enable=True):
         self._check(self.lib.selbm_timers(self.h, int(enable)))

@@ -58,6 +58,8 @@ struct selbm {
   double *d_acc = nullptr;
   int *d_flag = nullptr, *d_nfb = nullptr;
   int wall_max = 0;
+  int n_wallpts = 0;             // wall points (element, node) over all elements
+  double *d_xg = nullptr;        // [G][dim] coordinates of unique nodes (uploaded on first use)
   // captured steps (slot 0: no pending filter, slot 1: filter pending), launched with
   // cudaGraphLaunch on the handle's stream
   bool graph_enabled = true;   // SELBM_NO_GRAPH=1 in the environment disables capture
@@ -199,6 +201,7 @@ cudaError_t upload_real(selbm *h) {
     woff[el + 1] = (int32_t)wp.size();
     h->wall_max = std::max(h->wall_max, woff[el + 1] - woff[el]);
   }
+  h->n_wallpts = (int)wp.size();
   WallPt<Real> *dw;
   if ((e = upload(&dw, wp))) return e; h->d_walls = dw; if (dw) h->allocs.push_back(dw);
   int32_t *q;
@@ -501,7 +504,7 @@ void selbm_destroy(selbm_t *h) {
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   for (void *p : h->allocs) cudaFree(p);
   void *own[] = {h->d_l2g, h->d_owner, h->d_bslot, h->d_bnode_g, h->d_bnode_off, h->d_bnode_slot, h->d_first,
-                 h->d_mass, h->d_partial, h->d_diag, h->d_io};
+                 h->d_mass, h->d_partial, h->d_diag, h->d_io, h->d_xg};
   for (void *p : own)
     if (p) cudaFree(p);
   delete h;
@@ -736,6 +739,88 @@ int selbm_diagnostics(selbm_t *h, double out[8]) {
   for (int k = 0; k < 3; ++k) out[1 + k] = tmp[1 + k];
   out[4] = tmp[4]; out[5] = tmp[6]; out[6] = h->dt; out[7] = h->time;
   if (tmp[5] > 0) return h->fail(SELBM_ERR_NONFINITE, "state holds non-finite values");
+  return SELBM_OK;
+}
+
+int selbm_wall_stress(selbm_t *h, const double dir[3], double *tau) {
+  if (!h || !dir || !tau) return SELBM_ERR_ARG;
+  if (!h->initialized) return h->fail(SELBM_ERR_STATE, "state not initialised");
+  const int dim = h->S.dim;
+  double d[3] = {dir[0], dir[1], dim == 3 ? dir[2] : 0.0}, nrm = 0;
+  for (int c = 0; c < dim; ++c) nrm += d[c] * d[c];
+  if (!(nrm > 0)) return h->fail(SELBM_ERR_ARG, "wall_stress: zero direction");
+  for (int c = 0; c < 3; ++c) d[c] /= std::sqrt(nrm);
+  *tau = 0.0;
+  if (h->n_wallpts == 0) return SELBM_OK;
+  int rc = finalize(h);
+  if (rc) return rc;
+  const size_t nl = h->nloc();
+  if ((rc = ensure_io(h, (nl * (1 + dim) + 2 * (size_t)h->n_wallpts) * 8))) return rc;
+  double *rho_l = h->d_io, *u_l = h->d_io + nl, *part = h->d_io + nl * (1 + dim);
+  const double mu = h->P.rho0 * h->P.nu;
+  cudaError_t e = h->prec == SELBM_FP64
+                      ? launch_moments<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, rho_l, u_l, h->stream)
+                      : launch_moments<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, rho_l, u_l, h->stream);
+  if (e == cudaSuccess)
+    e = h->prec == SELBM_FP64
+            ? launch_wall_stress<double>(u_l, dim, h->S.n1, h->S.Np, h->S.E, h->S.affine, (const double *)h->d_el_drdx,
+                                         (const double *)h->d_drdx, (const double *)h->d_D, h->d_walls, h->d_wall_off, d,
+                                         mu, part, h->stream)
+            : launch_wall_stress<float>(u_l, dim, h->S.n1, h->S.Np, h->S.E, h->S.affine, (const float *)h->d_el_drdx,
+                                        (const float *)h->d_drdx, (const float *)h->d_D, h->d_walls, h->d_wall_off, d,
+                                        mu, part, h->stream);
+  std::vector<double> hp(2 * (size_t)h->n_wallpts);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), part, hp.size() * 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "wall_stress");
+  double num = 0, den = 0;
+  for (int k = 0; k < h->n_wallpts; ++k) { num += hp[2 * k]; den += hp[2 * k + 1]; }
+  *tau = den > 0 ? num / den : 0.0;
+  return SELBM_OK;
+}
+
+int selbm_radial_profile(selbm_t *h, const double origin[3], const double axis[3], double radius, int nbins,
+                         double *mean, double *mass) {
+  if (!h || !origin || !axis || !mean || !mass) return SELBM_ERR_ARG;
+  if (!h->initialized) return h->fail(SELBM_ERR_STATE, "state not initialised");
+  if (nbins < 1 || nbins > SELBM_PROFILE_MAX_BINS) return h->fail(SELBM_ERR_ARG, "radial_profile: nbins out of range");
+  if (!(radius > 0)) return h->fail(SELBM_ERR_ARG, "radial_profile: radius must be positive");
+  const int dim = h->S.dim;
+  double a[3] = {axis[0], axis[1], dim == 3 ? axis[2] : 0.0}, nrm = 0;
+  for (int c = 0; c < dim; ++c) nrm += a[c] * a[c];
+  if (!(nrm > 0)) return h->fail(SELBM_ERR_ARG, "radial_profile: zero axis");
+  for (int c = 0; c < 3; ++c) a[c] /= std::sqrt(nrm);
+  const double o[3] = {origin[0], origin[1], dim == 3 ? origin[2] : 0.0};
+  int rc = finalize(h);
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  if (!h->d_xg) {
+    std::vector<double> xg((size_t)h->S.G * dim);
+    for (int g = 0; g < h->S.G; ++g)
+      for (int c = 0; c < dim; ++c) xg[(size_t)g * dim + c] = h->S.X[(size_t)h->S.first_copy[g] * dim + c];
+    e = upload(&h->d_xg, xg);
+    if (e != cudaSuccess) return h->cuda_fail(e, "radial_profile");
+  }
+  const size_t nl = h->nloc();
+  const int blocks = 256;
+  if ((rc = ensure_io(h, (nl * (1 + dim) + (size_t)blocks * 2 * nbins) * 8))) return rc;
+  double *rho_l = h->d_io, *u_l = h->d_io + nl, *part = h->d_io + nl * (1 + dim);
+  e = h->prec == SELBM_FP64
+          ? launch_moments<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, rho_l, u_l, h->stream)
+          : launch_moments<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, rho_l, u_l, h->stream);
+  if (e == cudaSuccess)
+    e = launch_radial_profile(u_l, dim, h->d_first, h->d_xg, h->d_mass, h->S.G, o, a, radius, nbins, blocks, part,
+                              h->stream);
+  std::vector<double> hp((size_t)blocks * 2 * nbins);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), part, hp.size() * 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "radial_profile");
+  for (int b = 0; b < nbins; ++b) {
+    double su = 0, sm = 0;
+    for (int k = 0; k < blocks; ++k) { su += hp[((size_t)k * nbins + b) * 2]; sm += hp[((size_t)k * nbins + b) * 2 + 1]; }
+    mean[b] = sm > 0 ? su / sm : 0.0;
+    mass[b] = sm;
+  }
   return SELBM_OK;
 }
 

@@ -120,6 +120,15 @@ inline bool split_compiled(int lat, int N) {
   return (lat == SELBM_D3Q19 && (N == 4 || N == 7)) || (lat == SELBM_D3Q27 && (N == 5 || N == 7));
 }
 
+// pipe statistics (selbm_stats.cu)
+template <typename Real>
+cudaError_t launch_wall_stress(const double *u, int dim, int n, int Np, int E, int affine, const Real *el_drdx,
+                               const Real *drdx, const Real *Dm, const void *walls, const int32_t *wall_off,
+                               const double dir[3], double mu, double *out, cudaStream_t s);
+cudaError_t launch_radial_profile(const double *u, int dim, const int32_t *first, const double *xg, const double *mass,
+                                  int G, const double origin[3], const double axis[3], double radius, int nbins,
+                                  int blocks, double *partial, cudaStream_t s);
+
 template <typename Real>
 cudaError_t launch_eps(const double *u, int dim, int n, int Np, int E, int affine, const Real *el_drdx, const Real *drdx,
                        const Real *el_J, const Real *wJ, const Real *gllw, const Real *Dm, double mu, double *partial,

@@ -243,6 +243,32 @@ def pipe_init(U_bulk, radius=1.0, length=10.0, noise=0.05, seed=1234, nmodes=24,
     return f
 
 
+def loglaw_uplus(y_plus, kappa=0.41, c_plus=5.0):
+    """Mean velocity of a turbulent wall layer in wall units (Sec. 4, pipe initial profile):
+    u+ = y+ in the viscous sublayer, (1/kappa) ln y+ + C+ in the inertial sublayer, switched where
+    the two branches meet (y+ ~ 11 for kappa = 0.41, C+ = 5) so that the profile is continuous."""
+    y = np.maximum(np.asarray(y_plus, float), 1e-300)
+    return np.minimum(y, np.log(y) / kappa + c_plus)
+
+
+def pipe_loglaw_init(u_tau, nu, radius=1.0, length=10.0, noise=0.05, seed=1234, nmodes=24, rho0=1.0):
+    """Pipe initial field of Sec. 4: axial velocity u_tau u+(y+) with y+ = (R - r) u_tau / nu from
+    ``loglaw_uplus``, plus the seeded smooth perturbation of ``pipe_init`` scaled by the centreline
+    velocity u_tau u+(R u_tau / nu)."""
+    base = pipe_init(1.0, radius=radius, length=length, noise=noise, seed=seed, nmodes=nmodes, rho0=rho0)
+    Uc = u_tau * float(loglaw_uplus(radius * u_tau / nu))
+
+    def f(x):
+        X, Y = x[:, 0], x[:, 1]
+        r = np.sqrt(X ** 2 + Y ** 2)
+        rho, up = base(x)                       # 2 (1 - r^2/R^2) + perturbation, per unit bulk velocity
+        u = up * Uc
+        u[:, 2] = u_tau * loglaw_uplus(np.clip(radius - r, 0.0, None) * u_tau / nu) + \
+            (up[:, 2] - 2.0 * np.clip(1.0 - r ** 2 / radius ** 2, 0.0, None)) * Uc
+        return rho, u
+    return f
+
+
 # ----------------------------------------------------------------------------
 # the configurations of the benchmark suite (sizes as stated for each case)
 # ----------------------------------------------------------------------------
