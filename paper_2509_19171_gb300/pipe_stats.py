@@ -15,16 +15,16 @@ import time
 
 import numpy as np
 
-from . import FP32DEV, from_case
+from . import FP32DEV, FP64, SelbmError, from_case
 
 
-def run(steps, every, nbins=48, precision=FP32DEV, n_axial=32):
+def run(steps, every, nbins=48, precision=FP32DEV, n_axial=32, init="loglaw"):
     import workloads as W
     case = W.pipe_case(n_axial=n_axial)
     R, u_tau = 1.0, 0.0025
     nu = case.nu
     s = from_case(case, precision=precision)
-    s.init_from(W.pipe_loglaw_init(u_tau, nu, radius=R, length=10.0))
+    s.init_from(W.pipe_loglaw_init(u_tau, nu, radius=R, length=10.0) if init == "loglaw" else case.init)
     hist = []
     acc_mean, acc_mass = np.zeros(nbins), np.zeros(nbins)
     t0 = time.time()
@@ -33,11 +33,15 @@ def run(steps, every, nbins=48, precision=FP32DEV, n_axial=32):
         if k > done:
             s.step(k - done)
             done = k
+        try:
+            d = s.diagnostics()
+        except SelbmError as err:
+            hist.append({"step": k, "diverged": str(err)})
+            break
         tau = s.wall_stress([0, 0, 1])
         mean, mass = s.radial_profile([0, 0, 0], [0, 0, 1], R, nbins)
         acc_mean += mean * mass
         acc_mass += mass
-        d = s.diagnostics()
         hist.append({"step": k, "time": float(d[7]), "tau_w_over_rho_utau2": tau / (1.0 * u_tau ** 2),
                      "kinetic_energy": float(d[4])})
     wall_s = time.time() - t0
@@ -59,13 +63,14 @@ def main():
     ap.add_argument("--every", type=int, default=2000)
     ap.add_argument("--nbins", type=int, default=48)
     ap.add_argument("--out", default="pipe_stats.json")
+    ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--init", default="loglaw", choices=["loglaw", "laminar"])
     args = ap.parse_args()
-    res = run(args.steps, args.every, args.nbins)
+    res = run(args.steps, args.every, args.nbins, precision=FP64 if args.fp64 else FP32DEV, init=args.init)
     with open(args.out, "w") as fh:
         json.dump(res, fh, indent=1)
     h = res["history"]
-    print(json.dumps({"t0_over_dt": res["t0_over_dt"], "wall_s": res["wall_s"],
-                      "tau_w_first": h[0]["tau_w_over_rho_utau2"], "tau_w_last": h[-1]["tau_w_over_rho_utau2"]}))
+    print(json.dumps({"t0_over_dt": res["t0_over_dt"], "wall_s": res["wall_s"], "first": h[0], "last": h[-1]}))
 
 
 if __name__ == "__main__":

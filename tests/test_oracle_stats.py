@@ -79,5 +79,6 @@ def test_loglaw_profile():
     up = W.loglaw_uplus(y)
     assert np.allclose(up[:2], y[:2])
     assert np.allclose(up[2:], np.log(y[2:]) / 0.41 + 5.0)
-    grid = np.linspace(1, 30, 3000)
+    grid = np.linspace(0, 30, 3000)
     assert np.abs(np.diff(W.loglaw_uplus(grid))).max() < 0.02
+    assert W.loglaw_uplus(0.0) == 0.0 and W.loglaw_uplus(1e-3) == 1e-3       # no-slip wall, viscous sublayer

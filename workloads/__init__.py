@@ -245,10 +245,18 @@ def pipe_init(U_bulk, radius=1.0, length=10.0, noise=0.05, seed=1234, nmodes=24,
 
 def loglaw_uplus(y_plus, kappa=0.41, c_plus=5.0):
     """Mean velocity of a turbulent wall layer in wall units (Sec. 4, pipe initial profile):
-    u+ = y+ in the viscous sublayer, (1/kappa) ln y+ + C+ in the inertial sublayer, switched where
-    the two branches meet (y+ ~ 11 for kappa = 0.41, C+ = 5) so that the profile is continuous."""
-    y = np.maximum(np.asarray(y_plus, float), 1e-300)
-    return np.minimum(y, np.log(y) / kappa + c_plus)
+    u+ = y+ in the viscous sublayer, (1/kappa) ln y+ + C+ in the inertial sublayer, switched at the
+    upper crossing y_c of the two branches (y_c = 10.80 for kappa = 0.41, C+ = 5), so that the
+    profile is continuous and u+ = 0 on the wall."""
+    lo, hi = 1.0, 100.0                        # y - ln(y)/kappa - C+ changes sign once in [1, 100]
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if mid - math.log(mid) / kappa - c_plus < 0:
+            lo = mid
+        else:
+            hi = mid
+    y = np.asarray(y_plus, float)
+    return np.where(y < hi, y, np.log(np.maximum(y, hi)) / kappa + c_plus)
 
 
 def pipe_loglaw_init(u_tau, nu, radius=1.0, length=10.0, noise=0.05, seed=1234, nmodes=24, rho0=1.0):
