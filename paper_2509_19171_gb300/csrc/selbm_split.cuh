@@ -233,99 +233,101 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   //      a task reads f^{s-1} lines from sf and replaces its own line of so (f^0 in,
   //      result out), which no other task touches
   if constexpr (AFFINE && TI::SW) {
-    // swizzled FP32 tile (N = 7): one warp per population, each thread two r-lines
-    // (i1, i2) and (i1, i2 + 4) that share their t-lines, so every t-line read from
-    // shared memory serves both; the s-lines of line B sit 4 planes below those of A
+    // swizzled FP32 tile (N = 7): one warp per population, one axis per pass.  A pass
+    // takes two adjacent lines along its axis into registers (8-byte loads, conflict-free
+    // on the swizzled tile), applies D and adds c_l (D f) into the population's slice of so,
+    // whose element-interior nodes start as A f^0; the r-pass adds the r-derivative and
+    // finishes the stage combination.  Every tile value is read once per axis.
     const int pl = tid >> 5, lane = tid & 31;
-    const int i1 = lane & 7, i2 = lane >> 3;                 // i2 in 0..3
+    const int x = lane & 7, y = lane >> 3;                    // lines (x, y) and (x, y + 4)
     if (pl < na) {
       const Real *fa = sf + pl * PS;
+      Real *oa = so + pl * PS;
       const Real c0 = cf[pl * DIM + 0], c1 = cf[pl * DIM + 1], c2 = cf[pl * DIM + 2];
-      const int ownA = TI::line(i1, i2), swz = TI::sw(i1);   // line B = ownA + 4 PL, same swizzle
-      Real accA[n], accB[n];
+      // s-pass (AX = 1) and t-pass (AX = 2): the lines along the axis at r-index xp, xp + 1
+      // and o (the remaining index), one pair per lane
+      // acc: so holds earlier passes' sums (add to it); otherwise so starts as A f^0 on
+      // element-interior nodes (stages 2, 3) and 0 elsewhere.  Selects, not branches.
+      auto pass = [&](auto ax, auto acc_c, Real c) {
+        constexpr int AX = decltype(ax)::value;
+        constexpr bool acc = decltype(acc_c)::value;
+        const int xp = 2 * (lane & 3), o = lane >> 2;          // lines (xp, o) and (xp + 1, o)
+        const bool oin = o > 0 && o < n - 1;
+        const Real A = use_f0 ? p.A : Real(0);
+        const bool k0 = acc || (use_f0 && oin && xp > 0), k1 = acc || (use_f0 && oin && xp + 1 < n - 1);
+        const Real a0 = acc ? Real(1) : A;
+        float2 d[n];
 #pragma unroll
-      for (int j = 0; j < n; ++j) { accA[j] = 0; accB[j] = 0; }
-      if (c0 != Real(0)) {
-        Real v[n];
-        load_line<Real, n>(fa + ownA, swz, v);
-#pragma unroll
-        for (int j = 0; j < n; ++j) {
-          Real d = 0;
-#pragma unroll
-          for (int k = 0; k < n; ++k) d += m.D[j * n + k] * v[k];
-          accA[j] = c0 * d;
-        }
-        load_line<Real, n>(fa + ownA + 4 * TI::PL, swz, v);
-#pragma unroll
-        for (int j = 0; j < n; ++j) {
-          Real d = 0;
-#pragma unroll
-          for (int k = 0; k < n; ++k) d += m.D[j * n + k] * v[k];
-          accB[j] = c0 * d;
-        }
-      }
-      if (c1 != Real(0)) {
-        // s-lines (k, i2) and (k, i2 + 4); coefficient c1 D[i1][k] for both
-        Real dr[n];
-        load_line<Real, n>(sD + i1 * n, 0, dr);
-        const Real *ya[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) ya[q] = fa + i2 * TI::PL + ((q ^ i2) << 3);
+        for (int j = 0; j < n; ++j) d[j] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < n; ++k) {
-          const Real sk = c1 * dr[k];
-          const Real *la = ya[k & 3] + ((k & 4) << 3);
-          Real w[n];
-          load_line<Real, n>(la, TI::sw(k), w);
-          axpy_line<Real, n>(accA, sk, w);
-          load_line<Real, n>(la + 4 * TI::PL, TI::sw(k), w);
-          axpy_line<Real, n>(accB, sk, w);
+          const float2 vk = *reinterpret_cast<const float2 *>(fa + (AX == 1 ? TI::at(xp, k, o) : TI::at(xp, o, k)));
+#pragma unroll
+          for (int j = 0; j < n; ++j) d[j] = __ffma2_rn(make_float2(m.D[j * n + k], m.D[j * n + k]), vk, d[j]);
         }
-      }
+        const float2 cc = make_float2(c, c);
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          float2 *dst = reinterpret_cast<float2 *>(oa + (AX == 1 ? TI::at(xp, j, o) : TI::at(xp, o, j)));
+          const float2 old = *dst;
+          float2 r = __fmul2_rn(cc, d[j]);
+          const bool jin = acc || (j > 0 && j < n - 1);
+          r.x = (k0 && jin) ? fmaf(a0, old.x, r.x) : r.x;
+          r.y = (k1 && jin) ? fmaf(a0, old.y, r.y) : r.y;
+          *dst = r;
+        }
+        __syncwarp();
+      };
+      if (c1 != Real(0)) pass(std::integral_constant<int, 1>{}, std::false_type{}, c1);
       if (c2 != Real(0)) {
-        // t-lines (i1, k): coefficients c2 D[i2][k] (line A) and c2 D[i2 + 4][k] (line B)
-        Real da[n], db[n];
-        load_line<Real, n>(sD + i2 * n, 0, da);
-        load_line<Real, n>(sD + (i2 + 4) * n, 0, db);
-        const Real *zb[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) zb[q] = fa + ((i1 ^ q) << 3);
-#pragma unroll
-        for (int k = 0; k < n; ++k) {
-          Real w[n];
-          load_line<Real, n>(zb[k & 3] + k * TI::PL, swz, w);
-          axpy_line<Real, n>(accA, c2 * da[k], w);
-          axpy_line<Real, n>(accB, c2 * db[k], w);
-        }
+        if (c1 != Real(0)) pass(std::integral_constant<int, 2>{}, std::true_type{}, c2);
+        else pass(std::integral_constant<int, 2>{}, std::false_type{}, c2);
       }
-      // stage combination of both lines, in place of their f^0
-      const Real Jw1 = p.el_J[e] * sw[i1];
-      auto finish = [&](Real (&acc)[n], int own, bool edge, Real Jwl) {
-        Real *ob = so + pl * PS + own;
+      const bool fresh = c1 == Real(0) && c2 == Real(0);     // so holds f^0 or nothing yet
+      // r-pass and stage combination, lines (x, y) and (x, y + 4)
+      const Real Jwx = p.el_J[e] * sw[x];
+      const int swz = TI::sw(x);
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int o = y + 4 * h;
+        const bool lin = x > 0 && x < n - 1 && o > 0 && o < n - 1;
+        const int own = TI::line(x, o);
+        Real v[n], acc[n];
+        load_line<Real, n>(fa + own, swz, v);
+        if (!fresh) {
+          load_line<Real, n>(oa + own, swz, acc);
+        } else if (use_f0 && lin) {
+          load_line<Real, n>(oa + own, swz, acc);
+          acc[0] = 0;
+          acc[n - 1] = 0;
+#pragma unroll
+          for (int j = 1; j < n - 1; ++j) acc[j] *= p.A;
+        } else {
+#pragma unroll
+          for (int j = 0; j < n; ++j) acc[j] = 0;
+        }
+        if (c0 != Real(0)) {
+#pragma unroll
+          for (int j = 0; j < n; ++j) {
+            Real d = 0;
+#pragma unroll
+            for (int k = 0; k < n; ++k) d += m.D[j * n + k] * v[k];
+            acc[j] += c0 * d;
+          }
+        }
+        const Real Jwl = Jwx * sw[o];
         Real res[n];
-        if (edge) {
+        if (!lin) {
 #pragma unroll
           for (int j = 0; j < n; ++j) res[j] = Jwl * m.w[j] * acc[j];
         } else {
-          Real v[n];
-          load_line<Real, n>(fa + own, swz, v);
           res[0] = Jwl * m.w[0] * acc[0];
           res[n - 1] = Jwl * m.w[n - 1] * acc[n - 1];
-          if (use_f0) {
-            Real f0l[n];
-            load_line<Real, n>(ob, swz, f0l);
 #pragma unroll
-            for (int j = 1; j < n - 1; ++j) res[j] = p.B * v[j] + acc[j] + p.A * f0l[j];
-          } else {
-#pragma unroll
-            for (int j = 1; j < n - 1; ++j) res[j] = p.B * v[j] + acc[j];
-          }
+          for (int j = 1; j < n - 1; ++j) res[j] = p.B * v[j] + acc[j];
         }
-        store_line<Real, n>(ob, swz, res);
-      };
-      const bool edge1 = i1 == 0 || i1 == n - 1;
-      finish(accA, ownA, edge1 || i2 == 0, Jw1 * sw[i2]);
-      finish(accB, ownA + 4 * TI::PL, edge1 || i2 + 4 == n - 1, Jw1 * sw[i2 + 4]);
+        store_line<Real, n>(oa + own, swz, res);
+      }
     }
   } else
   {
