@@ -668,6 +668,53 @@ __device__ __forceinline__ void dense_vals(Real (&v)[n], const Real *M) {
   for (int j = 0; j < n; ++j) v[j] = o[j];
 }
 
+// y <- (M x M x M) y on NP populations of a tile, M (row-major) and its transpose MT in
+// shared memory.  On the swizzled FP32 tile the s- and t-passes take two adjacent columns
+// per task (8-byte accesses) and accumulate the columns of M with packed FMAs.
+template <typename Real, int n, int NP, int T>
+__device__ __forceinline__ void tile_dense3(Real *sf, int tid, const Real *M, const Real *MT) {
+  using TI = Tile<Real, n, 3>;
+  if constexpr (!TI::SW) {
+    tile_pass3<Real, n, NP, T>(sf, tid, [&](Real (&v)[n]) { dense_vals<Real, n>(v, M); });
+  } else {
+    constexpr int NL = n * n, PS = TI::PS;
+    for (int t = tid; t < NP * NL; t += T) {          // r-lines
+      const int a = t / NL, L = t - a * NL;
+      const int i1 = L % n, i2 = L / n;
+      Real v[n];
+      Real *base = sf + a * PS + TI::line(i1, i2);
+      load_line<Real, n>(base, TI::sw(i1), v);
+      dense_vals<Real, n>(v, M);
+      store_line<Real, n>(base, TI::sw(i1), v);
+    }
+    __syncthreads();
+    auto pair_pass = [&](auto addr) {
+      for (int t = tid; t < NP * NL / 2; t += T) {
+        const int a = t / (NL / 2), r = t - a * (NL / 2), q = r & 3, w = r >> 2;
+        Real *base = sf + a * PS;
+        float2 d[n];
+#pragma unroll
+        for (int j = 0; j < n; ++j) d[j] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+          const float2 vk = *reinterpret_cast<const float2 *>(base + addr(w, k, q));
+          Real col[n];
+          load_line<Real, n>(MT + k * n, 0, col);
+#pragma unroll
+          for (int j = 0; j < n; ++j) d[j] = __ffma2_rn(make_float2(col[j], col[j]), vk, d[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < n; ++j) *reinterpret_cast<float2 *>(base + addr(w, j, q)) = d[j];
+      }
+    };
+    // s-lines (i0 pair, k, i2 = w) and t-lines (i0 pair, i1 = w, k)
+    pair_pass([](int w, int k, int q) { return TI::line(k, w) + ((2 * q) ^ TI::sw(k)); });
+    __syncthreads();
+    pair_pass([](int w, int k, int q) { return TI::line(w, k) + ((2 * q) ^ TI::sw(w)); });
+    __syncthreads();
+  }
+}
+
 template <typename Real, int LAT, int n, bool AFFINE, int MODE>
 __global__ void __launch_bounds__(kProThreads, sizeof(Real) == 4 ? (MODE == PRO_LEARNED ? 3 : 4) : 1)
 prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedIn<Real, n> c) {
@@ -867,9 +914,10 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
         for (int q = 0; q < n; ++q) s += sVm[rr * n + q] * ssig[q] * sM1[q * n + jj];
         if (rr == 0 || rr == n - 1) s = (rr == jj) ? Real(1) : Real(0);
         sM0[k] = s;
+        sW[jj * n + rr] = s;                            // F_e^T
       }
       __syncthreads();
-      tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { dense_vals<Real, n>(v, sM0); });
+      tile_dense3<Real, n, Q, T>(sf, tid, sM0, sW);
     }
   } else if (MODE == PRO_FIXED) {
     // U and W are the same for every element: read them as kernel-parameter constants
