@@ -87,7 +87,8 @@ def workload(name, n=16):
 
 def counts(case, info):
     """Unique / interior / boundary node counts and bytes-per-launch model of the
-    unique-node layout ('Algorithmic bytes')."""
+    unique-node layout: every unique value a launch needs is read once and every value it
+    produces is written once."""
     E, N, dim = case.mesh.nelem, case.order, case.mesh.dim
     n = N + 1
     Np = n ** dim
@@ -125,7 +126,9 @@ def launches_per_step(split, learned):
 
 
 def flops_per_step(case, e_nonzero_axes, Q):
-    """Algorithmic FP operations of the stage kernels per step."""
+    """Algorithmic FP operations of the stage kernels per step: per node-population and stage
+    2(N+1) per non-zero derivative axis, 2 per axis for the metric combination and 5 for the
+    stage combination; stage 1 adds 20 (collision) and 2 d (N+1) (dense filter)."""
     E, N, dim = case.mesh.nelem, case.order, case.mesh.dim
     pops = E * (N + 1) ** dim * Q
     n = N + 1

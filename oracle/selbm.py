@@ -12,7 +12,7 @@ The state lives on unique (assembled) GLL nodes: f[Q, G].  The
 continuous-Galerkin coupling is the assembly (direct stiffness summation) of
 the element contributions, divided by the assembled lumped mass.
 
-Readings of the paper taken here (each one listed in the design doc):
+Readings of the paper taken here, where it is silent or garbled:
 * L f = M^{-1}(R (n.j) - C f) + F*: the identity term printed in the
   operator definition is dropped (it would create mass).
 * "3rd order SSP RK" is the Shu-Osher three-stage scheme.
@@ -21,7 +21,9 @@ Readings of the paper taken here (each one listed in the design doc):
 * The filter is applied once per step after the last stage, element by
   element; the copies of a shared node are reconciled by their
   mass-weighted average (they agree when every element has the same filter).
-* F = rho g with rho from the step's moments, frozen through the stages.
+* F = rho g with rho from the step's moments, frozen through the stages;
+  a per-node acceleration field (the pipe's perturbation force) enters the
+  same way, with its time factor taken at the start of the step.
 """
 import numpy as np
 
@@ -63,6 +65,27 @@ class OracleSELBM:
         self.set_filter(f)
         g = np.zeros(self.dim) if body_accel is None else np.asarray(body_accel, float)[: self.dim]
         self.g = g
+        self.fS = None                                           # extra per-node acceleration field
+        self.time = 0.0
+
+    def set_force_field(self, S, period, t_end):
+        """Extra body acceleration A(t) S_g on unique nodes (Sec. 4, pipe: the perturbation
+        force switched on for the first t_end of the run).  S [G, d]; A(t) = sin(2 pi t / period)
+        for t < t_end and 0 after; period <= 0 keeps A = 1 while t < t_end.  The time is the
+        time at the start of the step, and the force is frozen through the step."""
+        self.fS = np.asarray(S, float)[:, : self.dim]
+        self.f_period, self.f_tend = float(period), float(t_end)
+
+    def amplitude(self, t):
+        if self.fS is None or not t < self.f_tend:
+            return 0.0
+        return 1.0 if self.f_period <= 0 else float(np.sin(2.0 * np.pi * t / self.f_period))
+
+    def accel(self):
+        """Body acceleration at every unique node at the current time: g + A(t) S_g."""
+        if self.fS is None:
+            return self.g[None, :]
+        return self.g[None, :] + self.amplitude(self.time) * self.fS
 
     # ------------------------------------------------------------------ setup
     def set_filter(self, f):
@@ -85,7 +108,7 @@ class OracleSELBM:
 
     def initial_state(self, rho, u):
         """f_bar at rest in equilibrium: f = f^eq, so f_bar = f^eq - dt/2 F** (Sec. 2.1)."""
-        F = rho[:, None] * self.g[None, :]
+        F = rho[:, None] * self.accel()
         _, Fss = force_split(self.e, self.t, u, F)
         return equilibrium(self.e, self.t, rho, u) - 0.5 * self.dt * Fss
 
@@ -99,7 +122,7 @@ class OracleSELBM:
 
         Returns (f*, F*) with F* the leading-order force for the streaming step."""
         rho, u = self.moments(f)
-        F = rho[:, None] * self.g[None, :]
+        F = rho[:, None] * self.accel()
         Fstar, Fss = force_split(self.e, self.t, u, F)
         feq_bar = equilibrium(self.e, self.t, rho, u) - 0.5 * self.dt * Fss
         fstar = f - (f - feq_bar) / (self.tau + 0.5) + self.dt * Fss
@@ -201,12 +224,14 @@ class OracleSELBM:
         f0, Fstar = self.collide(f)
         f3 = self.ssprk3(f0, Fstar)
         sig, _, _ = self.learned_sigma(f3, params, lo, hi)
+        self.time += self.dt
         return self.apply_filter_elements(f3, sig)
 
     # ------------------------------------------------------------------- step
     def step(self, f):
         f0, Fstar = self.collide(f)
         f3 = self.ssprk3(f0, Fstar)
+        self.time += self.dt
         return self.apply_filter(f3)
 
     def run(self, f, nsteps):
