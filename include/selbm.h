@@ -153,6 +153,20 @@ int selbm_moments(selbm_t *h, double *rho, double *u, int on_device);
 int selbm_set_filter(selbm_t *h, const selbm_filter *filter);
 /* Replace the body acceleration g (F = rho g). */
 int selbm_set_body_force(selbm_t *h, const double g[3]);
+/*
+ * Per-node body acceleration field on top of g (Sec. 4, pipe flow: the divergence-free
+ * perturbation force F' of the first three eddy turnover times, applied through the same
+ * force split as the body force).  The acceleration at unique node x_g becomes
+ * g + A(t) S_g, with A(t) = sin(2 pi t / period) while t < t_end and 0 afterwards
+ * (period <= 0: A = 1 while t < t_end).  t is the time at the start of a step (the clock
+ * of selbm_info, reset by selbm_init) and the force is frozen through the step.
+ * S: host buffer [E][Np][dim] FP64 in acceleration units, copied; copies of a shared node
+ * take the value of their first copy (lowest e, then lowest local index).  S = NULL
+ * removes the field.  Takes effect from the next step and in selbm_init.  The first call
+ * allocates 3 G reals of device memory, freed by selbm_destroy.  Errors: SELBM_ERR_ARG
+ * (h NULL, period or t_end NaN), SELBM_ERR_CUDA (allocation or copy failure).
+ */
+int selbm_set_force_field(selbm_t *h, const double *S, double period, double t_end);
 
 /*
  * Diagnostics of the current (filtered) state, FP64 quadrature sums:

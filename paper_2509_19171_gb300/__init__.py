@@ -26,7 +26,8 @@ ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_MESH", -3: "ERR_CUDA", -4: "ERR_NONFI
 # functions declared in include/selbm.h (checked by the ABI test)
 EXPORTS = ["selbm_create", "selbm_destroy", "selbm_last_error", "selbm_info", "selbm_lattice_table",
            "selbm_node_coords", "selbm_init", "selbm_set_state", "selbm_get_state", "selbm_step",
-           "selbm_moments", "selbm_set_filter", "selbm_set_body_force", "selbm_diagnostics", "selbm_sync",
+           "selbm_moments", "selbm_set_filter", "selbm_set_body_force", "selbm_set_force_field",
+           "selbm_diagnostics", "selbm_sync",
            "selbm_wall_stress", "selbm_radial_profile",
            "selbm_mesh_check", "selbm_timers", "selbm_timers_read", "selbm_set_learned_filter",
            "selbm_clear_learned_filter", "selbm_learned_status", "selbm_element_sigma", "selbm_features",
@@ -83,6 +84,7 @@ def load_library(path: str = LIB_PATH):
     lib.selbm_moments.argtypes = [P, P, P, I]
     lib.selbm_set_filter.argtypes = [P, C.POINTER(FilterC)]
     lib.selbm_set_body_force.argtypes = [P, D]
+    lib.selbm_set_force_field.argtypes = [P, P, C.c_double, C.c_double]
     lib.selbm_diagnostics.argtypes = [P, D]
     lib.selbm_wall_stress.argtypes = [P, D, D]
     lib.selbm_radial_profile.argtypes = [P, D, D, C.c_double, I, D, D]
@@ -270,6 +272,17 @@ class SELBM:
         a = np.zeros(3)
         a[: len(g)] = g
         self._check(self.lib.selbm_set_body_force(self.h, _dptr(a)))
+
+    def set_force_field(self, S, period, t_end):
+        """Per-node acceleration A(t) S added to g (selbm_set_force_field).  S is an array
+        [E, Np, dim] or a function of the node coordinates x[n, dim] -> [n, dim]."""
+        if callable(S):
+            S = S(self.node_coords().reshape(-1, self.dim))
+        a = np.ascontiguousarray(np.asarray(S, np.float64).reshape(self.E, self.Np, -1)[..., : self.dim])
+        self._check(self.lib.selbm_set_force_field(self.h, _dptr(a), float(period), float(t_end)))
+
+    def clear_force_field(self):
+        self._check(self.lib.selbm_set_force_field(self.h, None, 0.0, 0.0))
 
     def diagnostics(self):
         out = np.zeros(8)

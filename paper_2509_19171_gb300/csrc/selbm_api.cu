@@ -60,6 +60,11 @@ struct selbm {
   int wall_max = 0;
   int n_wallpts = 0;             // wall points (element, node) over all elements
   double *d_xg = nullptr;        // [G][dim] coordinates of unique nodes (uploaded on first use)
+  // per-node acceleration field A(t) S_g added to g (allocated on first use)
+  bool field_on = false;
+  double f_period = 0.0, f_tend = 0.0, ft_host = 0.0;
+  void *d_fS = nullptr, *d_famp = nullptr;   // [3][G] S; [1] A(t) of the current step
+  double *d_ft = nullptr;                    // [1] time at the start of the next step
   // captured steps (slot 0: no pending filter, slot 1: filter pending), launched with
   // cudaGraphLaunch on the handle's stream
   bool graph_enabled = true;   // SELBM_NO_GRAPH=1 in the environment disables capture
@@ -226,6 +231,8 @@ KParams<Real> base_params(selbm *h) {
   p.bnode_g = h->d_bnode_g; p.bnode_off = h->d_bnode_off; p.bnode_slot = h->d_bnode_slot;
   p.bnode_minv = (const Real *)h->d_minv;
   p.T = (Real *)h->T; p.rho = (Real *)h->RHO;
+  p.fS = h->field_on ? (const Real *)h->d_fS : nullptr;
+  p.famp = (const Real *)h->d_famp;
   return p;
 }
 
@@ -354,6 +361,12 @@ cudaError_t enqueue_step_split(selbm *h, bool apply_filter) {
 // one time step: three stages, each = element kernel + assembly kernel
 template <typename Real>
 cudaError_t enqueue_step(selbm *h, bool apply_filter) {
+  if (h->field_on) {
+    // time factor of the acceleration field for this step (device clock, so that graph
+    // replays advance it)
+    cudaError_t e = launch_force_amp<Real>(h->d_ft, (Real *)h->d_famp, h->dt, h->f_period, h->f_tend, h->stream);
+    if (e != cudaSuccess) return e;
+  }
   KParams<Real> p = base_params<Real>(h);
   if (h->use_split) return enqueue_step_split<Real>(h, apply_filter);
   Real *FA = (Real *)h->FA, *F0 = (Real *)h->F0, *F2 = (Real *)h->F2;
@@ -552,9 +565,17 @@ int selbm_init(selbm_t *h, const double *rho, const double *u, int on_device) {
     drho = h->d_io; du = h->d_io + nl;
   }
   double g[3] = {h->P.body_accel[0], h->P.body_accel[1], h->P.body_accel[2]};
+  // the acceleration field enters the initial state with its time factor at t = 0
+  const double amp0 = !h->field_on || !(0.0 < h->f_tend) ? 0.0 : (h->f_period > 0.0 ? 0.0 : 1.0);
   cudaError_t e = h->prec == SELBM_FP64
-                      ? launch_init<double>(h->lat, drho, du, h->d_first, h->S.G, h->P.rho0, 0.5 * h->dt, g, h->has_force, (double *)h->FA, h->stream)
-                      : launch_init<float>(h->lat, drho, du, h->d_first, h->S.G, h->P.rho0, 0.5 * h->dt, g, h->has_force, (float *)h->FA, h->stream);
+                      ? launch_init<double>(h->lat, drho, du, h->d_first, h->S.G, h->P.rho0, 0.5 * h->dt, g, h->has_force,
+                                            h->field_on ? (const double *)h->d_fS : nullptr, amp0, (double *)h->FA, h->stream)
+                      : launch_init<float>(h->lat, drho, du, h->d_first, h->S.G, h->P.rho0, 0.5 * h->dt, g, h->has_force,
+                                           h->field_on ? (const float *)h->d_fS : nullptr, amp0, (float *)h->FA, h->stream);
+  if (e == cudaSuccess && h->d_ft) {
+    h->ft_host = 0.0;
+    e = cudaMemcpyAsync(h->d_ft, &h->ft_host, sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "init");
   h->initialized = true; h->filter_pending = false; h->steps = 0; h->time = 0.0;
@@ -698,7 +719,45 @@ int selbm_set_filter(selbm_t *h, const selbm_filter *f) {
 int selbm_set_body_force(selbm_t *h, const double g[3]) {
   if (!h || !g) return SELBM_ERR_ARG;
   for (int k = 0; k < 3; ++k) h->P.body_accel[k] = g[k];
-  h->has_force = g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0;
+  h->has_force = g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0 || h->field_on;
+  h->invalidate_graph();
+  return SELBM_OK;
+}
+
+int selbm_set_force_field(selbm_t *h, const double *S, double period, double t_end) {
+  if (!h) return SELBM_ERR_ARG;
+  const double *ga = h->P.body_accel;
+  if (!S) {
+    h->field_on = false;
+    h->has_force = ga[0] != 0.0 || ga[1] != 0.0 || ga[2] != 0.0;
+    h->invalidate_graph();
+    return SELBM_OK;
+  }
+  if (std::isnan(period) || std::isnan(t_end)) return h->fail(SELBM_ERR_ARG, "force field period / t_end is NaN");
+  const size_t G = (size_t)h->S.G, nl = h->nloc(), d = h->S.dim;
+  cudaError_t e = cudaSuccess;
+  if (!h->d_fS) {
+    if ((e = cudaMalloc(&h->d_fS, 3 * G * h->rsz)) != cudaSuccess) return h->cuda_fail(e, "force field alloc");
+    h->allocs.push_back(h->d_fS);
+    if ((e = cudaMalloc(&h->d_famp, 16)) != cudaSuccess) return h->cuda_fail(e, "force field alloc");
+    h->allocs.push_back(h->d_famp);
+    if ((e = cudaMalloc((void **)&h->d_ft, sizeof(double))) != cudaSuccess) return h->cuda_fail(e, "force field alloc");
+    h->allocs.push_back(h->d_ft);
+  }
+  int rc = ensure_io(h, nl * d * sizeof(double));
+  if (rc) return rc;
+  e = cudaMemcpyAsync(h->d_io, S, nl * d * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = h->prec == SELBM_FP64 ? launch_force_field<double>(h->d_io, h->d_first, (int)G, (int)d, (double *)h->d_fS, h->stream)
+                              : launch_force_field<float>(h->d_io, h->d_first, (int)G, (int)d, (float *)h->d_fS, h->stream);
+  h->ft_host = h->time;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_ft, &h->ft_host, sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "force field");
+  h->f_period = period;
+  h->f_tend = t_end;
+  h->field_on = true;
+  h->has_force = true;
   h->invalidate_graph();
   return SELBM_OK;
 }

@@ -258,14 +258,16 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
       });
       const Real rho = p.rho0 + drho;
       const Real inv = Real(1) / rho;
+      const size_t gid = l2g[i];
+      Real ga[3];
+      node_accel(p, gid, ga);
       Real u[3] = {0, 0, 0}, F[3] = {0, 0, 0}, uu = 0, uF = 0;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
         u[k] = j[k] * inv;
         uu += u[k] * u[k];
-        if (p.has_force) { F[k] = rho * p.g[k]; uF += u[k] * F[k]; }
+        if (p.has_force) { F[k] = rho * ga[k]; uF += u[k] * F[k]; }
       }
-      const size_t gid = l2g[i];
       const bool own = p.owner[(size_t)e * Np + i] != 0;
       const Real base = Real(1.5) * uu;
       static_for<0, Q>([&](auto ac) {
@@ -478,18 +480,33 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
         const Real rg = p.has_force ? rho[gid] : Real(0);
         const Real *f0p = f0 + gid;
         Real *fo = fout + gid;
+        // B dt F*_a / rho, with the per-node acceleration field: + B dt 3 t_a e_a . (A S_g)
+        Real sx[3] = {0, 0, 0};
+        const bool field = p.fS != nullptr;
+        if (field) {
+          const Real A = *p.famp;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) sx[k] = A * p.fS[(size_t)k * G + gid];
+        }
+        auto force = [&](int a) -> Real {
+          if (!field) return sfc[a] * rg;
+          Real es = 0;
+#pragma unroll
+          for (int k = 0; k < DIM; ++k) es += Real(V.e[a][k]) * sx[k];
+          return (sfc[a] + p.B * p.dt * Real(V.t[a]) * Real(3) * es) * rg;
+        };
         if (p.stage != 1) {
 #pragma unroll
           for (int a = 0; a < Q; ++a) {
             Real out = sf[a * PS + ti] + p.A * f0p[(size_t)a * G];
-            if (p.has_force) out += sfc[a] * rg;
+            if (p.has_force) out += force(a);
             fo[(size_t)a * G] = out;
           }
         } else {
 #pragma unroll
           for (int a = 0; a < Q; ++a) {
             Real out = sf[a * PS + ti];
-            if (p.has_force) out += sfc[a] * rg;
+            if (p.has_force) out += force(a);
             fo[(size_t)a * G] = out;
           }
         }

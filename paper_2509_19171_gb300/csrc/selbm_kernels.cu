@@ -103,16 +103,18 @@ __device__ void collide_node(Real *sf, int i, const KParams<Real> &p, Real *srho
   }
   const Real rho = p.rho0 + drho;
   const Real inv = Real(1) / rho;
+  const size_t gid = p.l2g[(size_t)e * Np + i];
+  Real ga[3];
+  node_accel(p, gid, ga);
   Real u[3] = {0, 0, 0}, F[3] = {0, 0, 0};
   Real uu = 0, uF = 0;
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
     u[k] = j[k] * inv;
     uu += u[k] * u[k];
-    if (p.has_force) { F[k] = rho * p.g[k]; uF += u[k] * F[k]; }
+    if (p.has_force) { F[k] = rho * ga[k]; uF += u[k] * F[k]; }
   }
   const Real ics2 = Real(3), ics4 = Real(9);
-  const size_t gid = p.l2g[(size_t)e * Np + i];
   const bool own = p.owner[(size_t)e * Np + i] != 0;
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
@@ -211,9 +213,11 @@ __global__ void __launch_bounds__(512) stage_kernel(const KParams<Real> p) {
       Real Fs = 0;
       if (p.has_force) {
         const Real rho_i = p.stage == 1 ? srho[i] : p.rho[gid];
+        Real ga[3];
+        node_accel(p, gid, ga);
         Real eg = 0;
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) eg += (Real)c_e[LAT][a][k] * p.g[k];
+        for (int k = 0; k < DIM; ++k) eg += (Real)c_e[LAT][a][k] * ga[k];
         Fs = wt<Real>(LAT, a) * eg * rho_i * ics2;
       }
       const Real fprev = sf[idx];
@@ -285,13 +289,15 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) dss_kernel(con
 #pragma unroll
       for (int a = 0; a < Q; ++a) s[a] += tc[a * EN];
     }
+    Real ga[3] = {0, 0, 0};
+    if (p.has_force) node_accel(p, gid, ga);
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
       Real Fs = 0;
       if (p.has_force) {
         Real eg = 0;
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) eg += (Real)c_e[LAT][a][k] * p.g[k];
+        for (int k = 0; k < DIM; ++k) eg += (Real)c_e[LAT][a][k] * ga[k];
         Fs = wt<Real>(LAT, a) * eg * rho * Real(3);
       }
       fout[(size_t)a * G + gid] = p.A * f0[(size_t)a * G + gid] + p.B * fin[(size_t)a * G + gid] + s[a] * minv + Bdt * Fs;
@@ -398,12 +404,15 @@ cudaError_t launch_finalize(int lat, const KParams<Real> &p, cudaStream_t s) {
 // f_bar = f^eq(rho, u) - dt/2 F** stored as g = f_bar - t rho0 (Sec. 2.1, f at equilibrium)
 template <typename Real, int LAT>
 __global__ void init_kernel(const double *rho, const double *u, const int32_t *first, int G, double rho0,
-                            double half_dt, double gx, double gy, double gz, int has_force, Real *out) {
+                            double half_dt, double gx, double gy, double gz, int has_force, const Real *fS,
+                            double amp, Real *out) {
   constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
     const size_t q = first[g];
     const double r = rho[q];
     double uv[3] = {0, 0, 0}, F[3] = {0, 0, 0}, gg[3] = {gx, gy, gz};
+    if (fS)
+      for (int k = 0; k < 3; ++k) gg[k] += amp * (double)fS[(size_t)k * G + g];
     double uu = 0, uF = 0;
     for (int k = 0; k < DIM; ++k) {
       uv[k] = u[q * DIM + k];
@@ -589,8 +598,40 @@ static int grid_for(size_t n, int threads) { return (int)std::min<size_t>((n + t
 
 template <typename Real>
 cudaError_t launch_init(int lat, const double *rho, const double *u, const int32_t *first, int G, double rho0,
-                        double half_dt, const double g[3], int has_force, Real *out, cudaStream_t s) {
-  SELBM_LAT_SWITCH(lat, (init_kernel<Real, L><<<grid_for(G, 256), 256, 0, s>>>(rho, u, first, G, rho0, half_dt, g[0], g[1], g[2], has_force, out)));
+                        double half_dt, const double g[3], int has_force, const Real *fS, double amp, Real *out,
+                        cudaStream_t s) {
+  SELBM_LAT_SWITCH(lat, (init_kernel<Real, L><<<grid_for(G, 256), 256, 0, s>>>(rho, u, first, G, rho0, half_dt, g[0], g[1], g[2], has_force, fS, amp, out)));
+  return cudaGetLastError();
+}
+
+// per-node acceleration field on unique nodes from the first local copy of each node
+template <typename Real>
+__global__ void force_field_kernel(const double *S, const int32_t *first, int G, int dim, Real *fS) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    const size_t q = first[g];
+    for (int k = 0; k < 3; ++k) fS[(size_t)k * G + g] = k < dim ? (Real)S[q * dim + k] : Real(0);
+  }
+}
+template <typename Real>
+cudaError_t launch_force_field(const double *S, const int32_t *first, int G, int dim, Real *fS, cudaStream_t s) {
+  force_field_kernel<Real><<<grid_for(G, 256), 256, 0, s>>>(S, first, G, dim, fS);
+  return cudaGetLastError();
+}
+
+// A(t) = sin(2 pi t / period) while t < t_end (1 for period <= 0), 0 after; t = ft[0] is the
+// time at the start of the step, advanced by dt here so that graph replays keep the clock
+template <typename Real>
+__global__ void force_amp_kernel(double *ft, Real *amp, double dt, double period, double t_end) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double t = ft[0];
+  double A = 0.0;
+  if (t < t_end) A = period > 0.0 ? sin(2.0 * 3.14159265358979323846 * t / period) : 1.0;
+  *amp = (Real)A;
+  ft[0] = t + dt;
+}
+template <typename Real>
+cudaError_t launch_force_amp(double *ft, Real *amp, double dt, double period, double t_end, cudaStream_t s) {
+  force_amp_kernel<Real><<<1, 32, 0, s>>>(ft, amp, dt, period, t_end);
   return cudaGetLastError();
 }
 template <typename Real>
@@ -618,7 +659,9 @@ cudaError_t launch_diag(int lat, const Real *buf, const double *mass, int G, dou
 
 #define SELBM_INST_UTIL(Real)                                                                                              \
   template cudaError_t launch_init<Real>(int, const double *, const double *, const int32_t *, int, double, double,      \
-                                         const double[3], int, Real *, cudaStream_t);                                    \
+                                         const double[3], int, const Real *, double, Real *, cudaStream_t);              \
+  template cudaError_t launch_force_field<Real>(const double *, const int32_t *, int, int, Real *, cudaStream_t);         \
+  template cudaError_t launch_force_amp<Real>(double *, Real *, double, double, double, cudaStream_t);                    \
   template cudaError_t launch_set_state<Real>(int, const double *, const int32_t *, int, size_t, double, Real *, cudaStream_t); \
   template cudaError_t launch_get_state<Real>(int, const Real *, const int32_t *, int, size_t, double, double *, cudaStream_t); \
   template cudaError_t launch_moments<Real>(int, const Real *, const int32_t *, int, size_t, double, double *, double *, cudaStream_t); \

@@ -46,7 +46,24 @@ struct KParams {
   Real *f0out;               // stage 1: f^0 written by owners
   Real *T;                   // assembly trace [Q][E*Nb]
   Real *rho;                 // [G] density of the step (forcing)
+  const Real *fS;            // [3][G] extra acceleration field S on unique nodes, or NULL
+  const Real *famp;          // [1] its time factor A(t) for the current step (device)
 };
+
+// body acceleration at unique node g: g + A(t) S_g (Sec. 4, pipe perturbation force)
+template <typename Real>
+__device__ __forceinline__ void node_accel(const KParams<Real> &p, size_t g, Real (&acc)[3]) {
+  acc[0] = p.g[0];
+  acc[1] = p.g[1];
+  acc[2] = p.g[2];
+  if (p.fS) {
+    const Real A = *p.famp;
+    const size_t G = (size_t)p.G;
+    acc[0] += A * p.fS[g];
+    acc[1] += A * p.fS[G + g];
+    acc[2] += A * p.fS[2 * G + g];
+  }
+}
 
 // Launchers (defined in selbm_kernels.cu).  lat = SELBM_D2Q9 / D3Q19 / D3Q27.
 template <typename Real>
@@ -59,7 +76,14 @@ cudaError_t launch_finalize(int lat, const KParams<Real> &p, cudaStream_t s);
 
 template <typename Real>
 cudaError_t launch_init(int lat, const double *rho, const double *u, const int32_t *first, int G, double rho0,
-                        double half_dt, const double g[3], int has_force, Real *out, cudaStream_t s);
+                        double half_dt, const double g[3], int has_force, const Real *fS, double amp, Real *out,
+                        cudaStream_t s);
+// per-node acceleration field: fS[k][g] = S[first[g]][k] (k < dim), 0 for k >= dim
+template <typename Real>
+cudaError_t launch_force_field(const double *S, const int32_t *first, int G, int dim, Real *fS, cudaStream_t s);
+// time factor of the field for the step starting at ft[0]; advances ft[0] by dt
+template <typename Real>
+cudaError_t launch_force_amp(double *ft, Real *amp, double dt, double period, double t_end, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_set_state(int lat, const double *f, const int32_t *first, int G, size_t nloc, double rho0, Real *out, cudaStream_t s);
 template <typename Real>

@@ -52,7 +52,7 @@ template <typename Real, int LAT, int n, bool AFFINE>
 constexpr size_t split_smem_bytes(int wall_max) {
   using S = SplitShape<LAT, n>;
   using TI = Tile<Real, n, 3>;
-  size_t reals = 2 * (size_t)S::PB * TI::PS + n * n + S::PB * 3 + S::PB + n;
+  size_t reals = 2 * (size_t)S::PB * TI::PS + n * n + S::PB * 3 + 2 * S::PB + n;
   if (!AFFINE) reals += (size_t)S::Np * 10;
   reals += (size_t)S::PB * wall_max;
   return reals * sizeof(Real);
@@ -115,8 +115,8 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   Real *so = sf + PB * PS;                          // [PB][PS] f^0 in, stage result out
   Real *sD = so + PB * PS;                          // [n][n]
   Real *cf = sD + n * n;                            // [PB][DIM] (affine: -B dt sum_k e_k dr_l/dx_k)
-  Real *fc = cf + PB * DIM;                         // [PB]      B dt F*_a / rho
-  Real *sw = fc + PB;                               // [n]
+  Real *fc = cf + PB * DIM;                         // [2][PB]   B dt F*_a / rho; B dt 3 t_a
+  Real *sw = fc + 2 * PB;                           // [n]
   Real *sg = sw + n;                                // curved: dr_l/dx_k [Np][9], wJ [Np]
   Real *wbuf = sg + (AFFINE ? 0 : Np * 10);         // [wall nodes][PB]
   const int e = blockIdx.x / NG, a0 = (blockIdx.x - e * NG) * PB;
@@ -192,6 +192,7 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
       if (aa == a) ta = Real(V.t[aa]);
     });
     fc[tid] = Bdt * ta * Real(3) * ge;
+    fc[PB + tid] = Bdt * ta * Real(3);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -497,11 +498,23 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
         if (b < 0) {
           const int g = l2g[i];
           Real *fo = p.fout + (size_t)a0 * G + g;
-          if (p.has_force) {
+          if (p.has_force && !p.fS) {
             const Real rg = p.rho[g];
 #pragma unroll
             for (int pl = 0; pl < PB; ++pl)
               if (pl < na) fo[pl * G] = sv[pl * PS] + fc[pl] * rg;
+          } else if (p.has_force) {
+            const Real rg = p.rho[g];
+            const Real A = *p.famp;                 // A(t) S_g of the per-node field
+            const Real sx[3] = {A * p.fS[g], A * p.fS[G + g], A * p.fS[2 * G + g]};
+#pragma unroll
+            for (int pl = 0; pl < PB; ++pl)
+              if (pl < na) {
+                const int a = a0 + pl;
+                const Real es = mask_sign<Real>(POS[0], NEG[0], a) * sx[0] + mask_sign<Real>(POS[1], NEG[1], a) * sx[1] +
+                                mask_sign<Real>(POS[2], NEG[2], a) * sx[2];
+                fo[pl * G] = sv[pl * PS] + (fc[pl] + fc[PB + pl] * es) * rg;
+              }
           } else if (full) {
 #pragma unroll
             for (int pl = 0; pl < PB; ++pl) fo[pl * G] = sv[pl * PS];
@@ -929,7 +942,6 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
   //      all elements, so copies agree), or element-interior nodes with the learned
   //      control, whose element-boundary copies go to the trace as wJ f for the
   //      mass-weighted assembly of shared nodes
-  const Real gacc[3] = {p.g[0], p.g[1], p.g[2]};
   const size_t EN = (size_t)p.E * p.Nb;
   for (int i = tid; i < Np; i += T) {
     const int ti = TI::node(i);
@@ -946,9 +958,10 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
     } else if (!p.owner[(size_t)e * Np + i]) {
       continue;
     }
-    Real fr[Q];
+    Real fr[Q], gacc[3];
 #pragma unroll
     for (int a = 0; a < Q; ++a) fr[a] = sf[a * PS + ti];
+    node_accel(p, g, gacc);
     const Real rho = bgk_collide<Real, LAT>(fr, p.rho0, p.omega, p.dt, p.half_dt, gacc, p.has_force != 0);
 #pragma unroll
     for (int a = 0; a < Q; ++a) p.f0out[(size_t)a * G + g] = fr[a];
@@ -962,7 +975,6 @@ template <typename Real, int LAT>
 __global__ void __launch_bounds__(256) dss_collide_kernel(const KParams<Real> p) {
   constexpr int Q = LT<LAT>::v.Q;
   const size_t EN = (size_t)p.E * p.Nb;
-  const Real gacc[3] = {p.g[0], p.g[1], p.g[2]};
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < p.Gb; u += gridDim.x * blockDim.x) {
     const int c0 = p.bnode_off[u], c1 = p.bnode_off[u + 1];
     const size_t gid = p.bnode_g[u];
@@ -977,6 +989,8 @@ __global__ void __launch_bounds__(256) dss_collide_kernel(const KParams<Real> p)
     }
 #pragma unroll
     for (int a = 0; a < Q; ++a) s[a] *= minv;
+    Real gacc[3];
+    node_accel(p, gid, gacc);
     const Real rho = bgk_collide<Real, LAT>(s, p.rho0, p.omega, p.dt, p.half_dt, gacc, p.has_force != 0);
 #pragma unroll
     for (int a = 0; a < Q; ++a) p.f0out[(size_t)a * p.G + gid] = s[a];
@@ -988,11 +1002,11 @@ __global__ void __launch_bounds__(256) dss_collide_kernel(const KParams<Real> p)
 template <typename Real, int LAT>
 __global__ void __launch_bounds__(256) collide_nodes_kernel(const KParams<Real> p) {
   constexpr int Q = LT<LAT>::v.Q;
-  const Real gacc[3] = {p.g[0], p.g[1], p.g[2]};
   for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < (size_t)p.G; g += (size_t)gridDim.x * blockDim.x) {
-    Real s[Q];
+    Real s[Q], gacc[3];
 #pragma unroll
     for (int a = 0; a < Q; ++a) s[a] = p.fin[(size_t)a * p.G + g];
+    node_accel(p, g, gacc);
     const Real rho = bgk_collide<Real, LAT>(s, p.rho0, p.omega, p.dt, p.half_dt, gacc, p.has_force != 0);
 #pragma unroll
     for (int a = 0; a < Q; ++a) p.f0out[(size_t)a * p.G + g] = s[a];

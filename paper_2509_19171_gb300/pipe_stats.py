@@ -1,5 +1,6 @@
 """Turbulent-pipe statistics run (Sec. 4): the butterfly pipe at Re_tau = 180 started from the
-log-law profile, driven by the body force g = 2 u_tau^2 / R, sampling the wall shear stress
+log-law profile, driven by the body force g = 2 u_tau^2 / R (with --peng also by the
+divergence-free perturbation force of the first three eddy turnover times), sampling the wall shear stress
 tau_w / (rho0 u_tau^2) and the space- and time-averaged axial velocity in wall units u+(y+).
 
 Every number comes from the library (steps, selbm_wall_stress, selbm_radial_profile); this
@@ -18,13 +19,17 @@ import numpy as np
 from . import FP32DEV, FP64, SelbmError, from_case
 
 
-def run(steps, every, nbins=48, precision=FP32DEV, n_axial=32, init="loglaw"):
+def run(steps, every, nbins=48, precision=FP32DEV, n_axial=32, init="loglaw", peng=False):
     import workloads as W
     case = W.pipe_case(n_axial=n_axial)
-    R, u_tau = 1.0, 0.0025
+    R, u_tau, L = 1.0, 0.0025, 10.0
     nu = case.nu
     s = from_case(case, precision=precision)
-    s.init_from(W.pipe_loglaw_init(u_tau, nu, radius=R, length=10.0) if init == "loglaw" else case.init)
+    if peng:
+        # perturbation force for the first 3 t0, period 8 t0, amplitude B0 g (g = 2 u_tau^2 / R)
+        t0 = R / u_tau
+        s.set_force_field(W.peng_forcing(2.0 * u_tau ** 2 / R, radius=R, length=L), 8.0 * t0, 3.0 * t0)
+    s.init_from(W.pipe_loglaw_init(u_tau, nu, radius=R, length=L) if init == "loglaw" else case.init)
     hist = []
     acc_mean, acc_mass = np.zeros(nbins), np.zeros(nbins)
     t0 = time.time()
@@ -65,8 +70,10 @@ def main():
     ap.add_argument("--out", default="pipe_stats.json")
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--init", default="loglaw", choices=["loglaw", "laminar"])
+    ap.add_argument("--peng", action="store_true", help="perturbation force for the first 3 t0")
     args = ap.parse_args()
-    res = run(args.steps, args.every, args.nbins, precision=FP64 if args.fp64 else FP32DEV, init=args.init)
+    res = run(args.steps, args.every, args.nbins, precision=FP64 if args.fp64 else FP32DEV, init=args.init,
+              peng=args.peng)
     with open(args.out, "w") as fh:
         json.dump(res, fh, indent=1)
     h = res["history"]

@@ -277,6 +277,38 @@ def pipe_loglaw_init(u_tau, nu, radius=1.0, length=10.0, noise=0.05, seed=1234, 
     return f
 
 
+def peng_forcing(g, radius=1.0, length=10.0, kz=3, ktheta=4, B0=50.0, kappa=0.5, l0=0.2, l=0.4):
+    """Spatial part of the pipe's divergence-free perturbation force (Sec. 4, after Peng et al.),
+    as an acceleration field for a pipe along z through the origin: the time factor
+    sin(2 pi t / P) is left out (it is applied per step).  In cylindrical components, with
+    phi = 2 pi (R - r - l0) / l and only inside l0 <= R - r <= l0 + l (l0, l in units of R):
+      F_r     = -g kappa B0 (R / r) (kz l / L) (1 - cos phi) cos(2 pi kz z / L) cos(ktheta theta)
+      F_theta =  g (1 - kappa) B0 (kz / ktheta) (2 pi R / L) sin phi cos(2 pi kz z / L) sin(ktheta theta)
+      F_z     = -g B0 (R / r) sin phi sin(2 pi kz z / L) cos(ktheta theta)
+    turned to Cartesian components.  The paper does not give kz and ktheta."""
+    R, L = float(radius), float(length)
+    L0, Lb = l0 * R, l * R
+
+    def f(x):
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        r = np.sqrt(X ** 2 + Y ** 2)
+        th = np.arctan2(Y, X)
+        inside = (R - r >= L0) & (R - r <= L0 + Lb)
+        rs = np.where(inside, r, R)                     # keeps R / r finite off the band
+        phi = 2.0 * np.pi * (R - rs - L0) / Lb
+        cz, sz = np.cos(2.0 * np.pi * kz * Z / L), np.sin(2.0 * np.pi * kz * Z / L)
+        ct, st = np.cos(ktheta * th), np.sin(ktheta * th)
+        Fr = -g * kappa * B0 * (R / rs) * (kz * Lb / L) * (1.0 - np.cos(phi)) * cz * ct
+        Ft = g * (1.0 - kappa) * B0 * (kz / ktheta) * (2.0 * np.pi * R / L) * np.sin(phi) * cz * st
+        Fz = -g * B0 * (R / rs) * np.sin(phi) * sz * ct
+        out = np.zeros((x.shape[0], 3))
+        out[:, 0] = np.where(inside, Fr * np.cos(th) - Ft * np.sin(th), 0.0)
+        out[:, 1] = np.where(inside, Fr * np.sin(th) + Ft * np.cos(th), 0.0)
+        out[:, 2] = np.where(inside, Fz, 0.0)
+        return out
+    return f
+
+
 # ----------------------------------------------------------------------------
 # the configurations of the benchmark suite (sizes as stated for each case)
 # ----------------------------------------------------------------------------
