@@ -281,26 +281,47 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) dss_kernel(con
     const size_t gid = p.bnode_g[u];
     const Real minv = p.bnode_minv[u];
     const Real rho = p.has_force ? p.rho[gid] : Real(0);
-    Real s[Q];
-#pragma unroll
-    for (int a = 0; a < Q; ++a) s[a] = 0;
-    for (int c = c0; c < c1; ++c) {
-      const Real *tc = Tr + p.bnode_slot[c];
-#pragma unroll
-      for (int a = 0; a < Q; ++a) s[a] += tc[a * EN];
-    }
     Real ga[3] = {0, 0, 0};
     if (p.has_force) node_accel(p, gid, ga);
+    // populations in two halves; two copies per iteration, their loads in flight together,
+    // added in ascending copy order
+    constexpr int QH = (Q + 1) / 2;
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      Real Fs = 0;
-      if (p.has_force) {
-        Real eg = 0;
+    for (int hh = 0; hh < 2; ++hh) {
+      const int a0 = hh * QH;
+      Real s[QH];
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) eg += (Real)c_e[LAT][a][k] * ga[k];
-        Fs = wt<Real>(LAT, a) * eg * rho * Real(3);
+      for (int a = 0; a < QH; ++a) s[a] = 0;
+      int c = c0;
+      for (; c + 1 < c1; c += 2) {
+        const Real *t0 = Tr + p.bnode_slot[c] + (size_t)a0 * EN, *t1 = Tr + p.bnode_slot[c + 1] + (size_t)a0 * EN;
+        Real v0[QH], v1[QH];
+#pragma unroll
+        for (int a = 0; a < QH; ++a)
+          if (a0 + a < Q) { v0[a] = t0[a * EN]; v1[a] = t1[a * EN]; }
+#pragma unroll
+        for (int a = 0; a < QH; ++a)
+          if (a0 + a < Q) { s[a] += v0[a]; s[a] += v1[a]; }
       }
-      fout[(size_t)a * G + gid] = p.A * f0[(size_t)a * G + gid] + p.B * fin[(size_t)a * G + gid] + s[a] * minv + Bdt * Fs;
+      if (c < c1) {
+        const Real *t0 = Tr + p.bnode_slot[c] + (size_t)a0 * EN;
+#pragma unroll
+        for (int a = 0; a < QH; ++a)
+          if (a0 + a < Q) s[a] += t0[a * EN];
+      }
+#pragma unroll
+      for (int al = 0; al < QH; ++al) {
+        const int a = a0 + al;
+        if (a >= Q) break;
+        Real Fs = 0;
+        if (p.has_force) {
+          Real eg = 0;
+#pragma unroll
+          for (int k = 0; k < DIM; ++k) eg += (Real)c_e[LAT][a][k] * ga[k];
+          Fs = wt<Real>(LAT, a) * eg * rho * Real(3);
+        }
+        fout[(size_t)a * G + gid] = p.A * f0[(size_t)a * G + gid] + p.B * fin[(size_t)a * G + gid] + s[al] * minv + Bdt * Fs;
+      }
     }
   }
 }
