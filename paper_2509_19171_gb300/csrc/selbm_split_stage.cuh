@@ -145,9 +145,19 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
     if (!AFFINE) {
       const unsigned s_g = (unsigned)__cvta_generic_to_shared(sg);
       const Real *gm = p.drdx + (size_t)e * Np * 9;
-      for (int c = tid; c < Np * 9; c += T) cp_async_s<Real>(s_g + c * RS, gm + c);
       const Real *wj = p.wJ + (size_t)e * Np;
-      for (int c = tid; c < Np; c += T) cp_async_s<Real>(s_g + (Np * 9 + c) * RS, wj + c);
+      if constexpr (TI::SW) {
+        // swizzled FP32 tile: metric component c of node i at c PS + node(i), wJ at 9 PS +
+        // node(i), so that the passes read them like the tile
+        for (int idx = tid; idx < Np * 9; idx += T) {
+          const int i = idx / 9, c = idx - i * 9;
+          cp_async_s<Real>(s_g + (c * PS + TI::node(i)) * RS, gm + idx);
+        }
+        for (int i = tid; i < Np; i += T) cp_async_s<Real>(s_g + (9 * PS + TI::node(i)) * RS, wj + i);
+      } else {
+        for (int c = tid; c < Np * 9; c += T) cp_async_s<Real>(s_g + c * RS, gm + c);
+        for (int c = tid; c < Np; c += T) cp_async_s<Real>(s_g + (Np * 9 + c) * RS, wj + c);
+      }
     }
   }
   // ---- per-element constants while the copies are in flight
@@ -215,18 +225,29 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   // ---- (population, r-line) tasks, ROUNDS per thread with the same r-line (i1, i2);
   //      a task reads f^{s-1} lines from sf and replaces its own line of so (f^0 in,
   //      result out), which no other task touches
-  if constexpr (AFFINE && TI::SW) {
+  if constexpr (TI::SW) {
     // swizzled FP32 tile (N = 7): one warp per population, one axis per pass.  A pass
     // takes two adjacent lines along its axis into registers (8-byte loads, conflict-free
     // on the swizzled tile), applies D and adds c_l (D f) into the population's slice of so,
     // whose element-interior nodes start as A f^0; the r-pass adds the r-derivative and
-    // finishes the stage combination.  Every tile value is read once per axis.
+    // finishes the stage combination.  Every tile value is read once per axis.  On curved
+    // elements c_l = -B dt sum_k e_k dr_l/dx_k is read per node from the metric planes.
     const int pl = tid >> 5, lane = tid & 31;
     const int x = lane & 7, y = lane >> 3;                    // lines (x, y) and (x, y + 4)
     if (pl < na) {
       const Real *fa = sf + pl * PS;
       Real *oa = so + pl * PS;
-      const Real c0 = cf[pl * DIM + 0], c1 = cf[pl * DIM + 1], c2 = cf[pl * DIM + 2];
+      Real c0 = 1, c1 = 1, c2 = 1;                            // curved: any non-zero marker
+      Real eb[3] = {0, 0, 0};                                 // curved: -B dt e_k
+      if constexpr (AFFINE) {
+        c0 = cf[pl * DIM + 0];
+        c1 = cf[pl * DIM + 1];
+        c2 = cf[pl * DIM + 2];
+      } else {
+        const int a = a0 + pl;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) eb[k] = -Bdt * mask_sign<Real>(POS[k], NEG[k], a);
+      }
       // s-pass (AX = 1) and t-pass (AX = 2): the lines along the axis at r-index xp, xp + 1
       // and o (the remaining index), one pair per lane
       // acc: so holds earlier passes' sums (add to it); otherwise so starts as A f^0 on
@@ -251,9 +272,21 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
         const float2 cc = make_float2(c, c);
 #pragma unroll
         for (int j = 0; j < n; ++j) {
-          float2 *dst = reinterpret_cast<float2 *>(oa + (AX == 1 ? TI::at(xp, j, o) : TI::at(xp, o, j)));
+          const int off = AX == 1 ? TI::at(xp, j, o) : TI::at(xp, o, j);
+          float2 *dst = reinterpret_cast<float2 *>(oa + off);
           const float2 old = *dst;
-          float2 r = __fmul2_rn(cc, d[j]);
+          float2 r;
+          if constexpr (AFFINE) {
+            r = __fmul2_rn(cc, d[j]);
+          } else {
+            // per-node coefficients of the pair: metric planes dr_AX/dx_k
+            float2 cn = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+              if (eb[k] != Real(0))
+                cn = __ffma2_rn(make_float2(eb[k], eb[k]), *reinterpret_cast<const float2 *>(sg + (AX * 3 + k) * PS + off), cn);
+            r = __fmul2_rn(cn, d[j]);
+          }
           const bool jin = acc || (j > 0 && j < n - 1);
           r.x = (k0 && jin) ? fmaf(a0, old.x, r.x) : r.x;
           r.y = (k1 && jin) ? fmaf(a0, old.y, r.y) : r.y;
@@ -268,7 +301,7 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
       }
       const bool fresh = c1 == Real(0) && c2 == Real(0);     // so holds f^0 or nothing yet
       // r-pass and stage combination, lines (x, y) and (x, y + 4)
-      const Real Jwx = p.el_J[e] * sw[x];
+      const Real Jwx = AFFINE ? p.el_J[e] * sw[x] : Real(0);
       const int swz = TI::sw(x);
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
@@ -289,23 +322,44 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
 #pragma unroll
           for (int j = 0; j < n; ++j) acc[j] = 0;
         }
+        Real cr[n];                                           // r-coefficient per node
+#pragma unroll
+        for (int j = 0; j < n; ++j) cr[j] = c0;
+        if constexpr (!AFFINE) {
+#pragma unroll
+          for (int j = 0; j < n; ++j) cr[j] = 0;
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+            if (eb[k] != Real(0)) {
+              Real mk[n];
+              load_line<Real, n>(sg + k * PS + own, swz, mk);
+#pragma unroll
+              for (int j = 0; j < n; ++j) cr[j] += eb[k] * mk[j];
+            }
+        }
         if (c0 != Real(0)) {
 #pragma unroll
           for (int j = 0; j < n; ++j) {
             Real d = 0;
 #pragma unroll
             for (int k = 0; k < n; ++k) d += m.D[j * n + k] * v[k];
-            acc[j] += c0 * d;
+            acc[j] += cr[j] * d;
           }
         }
-        const Real Jwl = Jwx * sw[o];
+        Real wl[n];                                           // wJ of the line's nodes
+        if constexpr (AFFINE) {
+#pragma unroll
+          for (int j = 0; j < n; ++j) wl[j] = Jwx * sw[o] * m.w[j];
+        } else {
+          load_line<Real, n>(sg + 9 * PS + own, swz, wl);
+        }
         Real res[n];
         if (!lin) {
 #pragma unroll
-          for (int j = 0; j < n; ++j) res[j] = Jwl * m.w[j] * acc[j];
+          for (int j = 0; j < n; ++j) res[j] = wl[j] * acc[j];
         } else {
-          res[0] = Jwl * m.w[0] * acc[0];
-          res[n - 1] = Jwl * m.w[n - 1] * acc[n - 1];
+          res[0] = wl[0] * acc[0];
+          res[n - 1] = wl[n - 1] * acc[n - 1];
 #pragma unroll
           for (int j = 1; j < n - 1; ++j) res[j] = p.B * v[j] + acc[j];
         }

@@ -183,14 +183,16 @@ def test_split_fp32_walls_every_face(P):
         assert rel(s.get_state(), o.to_local(f)) <= 1e-6
 
 
-def test_split_fp32_curved_pipe(P):
+@pytest.mark.parametrize("N", [4, 7])
+def test_split_fp32_curved_pipe(P, N):
     """FP32 curved elements (per-node metrics), flux bounce-back and body force in the
-    split form, D3Q19 N = 4, within 1e-6 of the FP64 oracle over two steps."""
-    mesh = W.pipe_mesh(n_core=2, n_radial=2, n_axial=2, length=1.0)
-    filt = {"shape": 0, "gamma": 0.1, "kc": 2.0}
+    split form, D3Q19 N = 4 and 7 (the paired-axis passes with metric planes), within 1e-6
+    of the FP64 oracle over two steps."""
+    mesh = W.pipe_mesh(n_core=2, n_radial=2, n_axial=2 if N == 4 else 1, length=1.0)
+    filt = {"shape": 0, "gamma": 0.1, "kc": float(N - 2)}
     g = (0.0, 0.0, 2e-4)
-    o = OracleSELBM(mesh, "D3Q19", 4, 2e-3, filt=filt, body_accel=g)
-    s = P.SELBM(mesh, "D3Q19", 4, 2e-3, precision=P.FP32DEV, filt=filt, body_accel=g)
+    o = OracleSELBM(mesh, "D3Q19", N, 2e-3, filt=filt, body_accel=g)
+    s = P.SELBM(mesh, "D3Q19", N, 2e-3, precision=P.FP32DEV, filt=filt, body_accel=g)
     assert s.split
     f = random_continuous_state(o, 0.02, 9)
     s.set_state(np.ascontiguousarray(o.to_local(f)))
