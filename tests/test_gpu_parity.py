@@ -221,3 +221,28 @@ def test_fp32_deviation_form(P):
     rho_g, u_g = s.moments()
     assert float(np.abs(rho_g - rho_o[o.glo]).max()) <= 1e-6
     assert float(np.abs(u_g - u_o[o.glo]).max()) <= 1e-4 * case.U0
+
+
+@pytest.mark.parametrize("tau", [0.1, 0.4])
+def test_poiseuille_walls_body_force(P, tau):
+    """Planar Poiseuille of the slip study (Sec. 3.3): 4 x 4 quads, N = 8, flux bounce-back
+    walls at y = 0, 1, body force G; the relaxation time tau = lambda / dt sets nu at the
+    CFL-0.5 step.  Started on the parabola, 100 steps: FP64 state within 1e-11 of the oracle,
+    and the wall slip the same on both sides."""
+    mesh = W.box_mesh((4, 4), (0, 0), (1, 1), (True, False), walls={2: 1, 3: 1}, wall_velocity=[[0, 0]])
+    probe = OracleSELBM(mesh, "D2Q9", 8, nu=1.0, cfl=0.5)
+    nu = tau * probe.dt / 3.0
+    umax = 0.1 / 3.0
+    G = 8 * nu * umax
+    init = W.poiseuille_init(G, nu)
+    o, s = pair(P, mesh, "D2Q9", 8, nu, g=(G, 0.0, 0.0), init=init)
+    f = o.run(o.initial_state_from(init), 100)
+    s.step(100)
+    assert rel(s.get_state(), o.to_local(f)) <= 1e-11
+    _, u = o.moments(f)
+    wall = np.abs(o.Xg[:, 1]) < 1e-12
+    _, ug = s.moments()
+    yl = s.node_coords()[..., 1].reshape(-1)
+    slip_o = np.abs(u[wall, 0]).max() / umax
+    slip_g = np.abs(ug.reshape(-1, 2)[np.abs(yl) < 1e-12, 0]).max() / umax
+    assert slip_o > 0 and abs(slip_g - slip_o) <= 1e-9 * max(slip_o, 1e-3)
