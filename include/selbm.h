@@ -151,6 +151,18 @@ int selbm_moments(selbm_t *h, double *rho, double *u, int on_device);
 
 /* Replace the filter (Sec. 2.4); takes effect from the next step. */
 int selbm_set_filter(selbm_t *h, const selbm_filter *filter);
+/*
+ * Time scheme of the streaming step (Sec. 2.2.2).  0 (default): the Shu-Osher three-stage
+ * SSPRK3 that the text names.  1: the four stages exactly as printed,
+ *   f1 = f0 + dt/3 L f0,  f2 = f1 - 3dt/4 L(f0 - f1),  f3 = f2 + 2dt/3 L(f0 - f1 + f2),
+ *   f  = f3 - dt/4 L(f0 - f1 + f2 - f3),
+ * f0 the collided state, L applied to each combination as a whole (its force and
+ * wall-velocity terms once per application); for a linear L (no force, walls at rest) this is
+ * the fourth-order Taylor polynomial of exp(dt L).  The first call with 1 allocates three
+ * more state arrays (3 Q G reals), freed by selbm_destroy.  Takes effect from the next step.
+ * Errors: SELBM_ERR_ARG (h NULL, scheme not 0 or 1), SELBM_ERR_CUDA (allocation failure).
+ */
+int selbm_set_time_scheme(selbm_t *h, int scheme);
 /* Replace the body acceleration g (F = rho g). */
 int selbm_set_body_force(selbm_t *h, const double g[3]);
 /*

@@ -67,6 +67,12 @@ class OracleSELBM:
         self.g = g
         self.fS = None                                           # extra per-node acceleration field
         self.time = 0.0
+        self.scheme = 0                                          # 0 Shu-Osher SSPRK3, 1 printed stages
+
+    def set_time_scheme(self, scheme):
+        """0: the Shu-Osher SSPRK3 that the text names; 1: the four stages as printed in
+        Sec. 2.2.2, with L applied to each stage combination as a whole."""
+        self.scheme = int(scheme)
 
     def set_force_field(self, S, period, t_end):
         """Extra body acceleration A(t) S_g on unique nodes (Sec. 4, pipe: the perturbation
@@ -171,6 +177,19 @@ class OracleSELBM:
         f2 = 0.75 * f0 + 0.25 * (f1 + dt * self.rhs(f1, Fstar))
         return f0 / 3.0 + 2.0 / 3.0 * (f2 + dt * self.rhs(f2, Fstar))
 
+    def rk_printed(self, f0, Fstar):
+        """The four stages as printed (Sec. 2.2.2):
+        f1 = f0 + dt/3 L f0,  f2 = f1 - 3dt/4 L(f0 - f1),  f3 = f2 + 2dt/3 L(f0 - f1 + f2),
+        f = f3 - dt/4 L(f0 - f1 + f2 - f3)."""
+        dt = self.dt
+        f1 = f0 + dt / 3.0 * self.rhs(f0, Fstar)
+        f2 = f1 - 0.75 * dt * self.rhs(f0 - f1, Fstar)
+        f3 = f2 + 2.0 / 3.0 * dt * self.rhs(f0 - f1 + f2, Fstar)
+        return f3 - 0.25 * dt * self.rhs(f0 - f1 + f2 - f3, Fstar)
+
+    def stream(self, f0, Fstar):
+        return self.ssprk3(f0, Fstar) if self.scheme == 0 else self.rk_printed(f0, Fstar)
+
     # ----------------------------------------------------------------- filter
     def assemble_average(self, fl):
         """Element copies [Q, E, Np] -> unique nodes: mass-weighted average sum_c wJ_c f_c / M.
@@ -222,7 +241,7 @@ class OracleSELBM:
     def step_learned(self, f, params, lo, hi):
         """One step whose end-of-step filter is chosen per element by the learned control."""
         f0, Fstar = self.collide(f)
-        f3 = self.ssprk3(f0, Fstar)
+        f3 = self.stream(f0, Fstar)
         sig, _, _ = self.learned_sigma(f3, params, lo, hi)
         self.time += self.dt
         return self.apply_filter_elements(f3, sig)
@@ -230,7 +249,7 @@ class OracleSELBM:
     # ------------------------------------------------------------------- step
     def step(self, f):
         f0, Fstar = self.collide(f)
-        f3 = self.ssprk3(f0, Fstar)
+        f3 = self.stream(f0, Fstar)
         self.time += self.dt
         return self.apply_filter(f3)
 

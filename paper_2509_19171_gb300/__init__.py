@@ -26,7 +26,7 @@ ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_MESH", -3: "ERR_CUDA", -4: "ERR_NONFI
 # functions declared in include/selbm.h (checked by the ABI test)
 EXPORTS = ["selbm_create", "selbm_destroy", "selbm_last_error", "selbm_info", "selbm_lattice_table",
            "selbm_node_coords", "selbm_init", "selbm_set_state", "selbm_get_state", "selbm_step",
-           "selbm_moments", "selbm_set_filter", "selbm_set_body_force", "selbm_set_force_field",
+           "selbm_moments", "selbm_set_filter", "selbm_set_body_force", "selbm_set_force_field", "selbm_set_time_scheme",
            "selbm_diagnostics", "selbm_sync",
            "selbm_wall_stress", "selbm_radial_profile",
            "selbm_mesh_check", "selbm_timers", "selbm_timers_read", "selbm_set_learned_filter",
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH):
     lib.selbm_set_filter.argtypes = [P, C.POINTER(FilterC)]
     lib.selbm_set_body_force.argtypes = [P, D]
     lib.selbm_set_force_field.argtypes = [P, P, C.c_double, C.c_double]
+    lib.selbm_set_time_scheme.argtypes = [P, I]
     lib.selbm_diagnostics.argtypes = [P, D]
     lib.selbm_wall_stress.argtypes = [P, D, D]
     lib.selbm_radial_profile.argtypes = [P, D, D, C.c_double, I, D, D]
@@ -280,6 +281,10 @@ class SELBM:
             S = S(self.node_coords().reshape(-1, self.dim))
         a = np.ascontiguousarray(np.asarray(S, np.float64).reshape(self.E, self.Np, -1)[..., : self.dim])
         self._check(self.lib.selbm_set_force_field(self.h, _dptr(a), float(period), float(t_end)))
+
+    def set_time_scheme(self, scheme):
+        """0: Shu-Osher SSPRK3 (default); 1: the four stages as printed (selbm_set_time_scheme)."""
+        self._check(self.lib.selbm_set_time_scheme(self.h, int(scheme)))
 
     def clear_force_field(self):
         self._check(self.lib.selbm_set_force_field(self.h, None, 0.0, 0.0))

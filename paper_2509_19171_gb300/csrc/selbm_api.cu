@@ -65,6 +65,9 @@ struct selbm {
   double f_period = 0.0, f_tend = 0.0, ft_host = 0.0;
   void *d_fS = nullptr, *d_famp = nullptr;   // [3][G] S; [1] A(t) of the current step
   double *d_ft = nullptr;                    // [1] time at the start of the next step
+  // time scheme: 0 Shu-Osher SSPRK3, 1 the printed four-stage form (extra stage buffers)
+  int scheme = 0;
+  void *S1 = nullptr, *S2 = nullptr, *SG = nullptr, *SB = nullptr;
   // captured steps (slot 0: no pending filter, slot 1: filter pending), launched with
   // cudaGraphLaunch on the handle's stream
   bool graph_enabled = true;   // SELBM_NO_GRAPH=1 in the environment disables capture
@@ -358,6 +361,73 @@ cudaError_t enqueue_step_split(selbm *h, bool apply_filter) {
   return cudaSuccess;
 }
 
+// one time step of the printed four-stage scheme (Sec. 2.2.2, taken literally):
+//   f1 = f0 + dt/3 L f0,  f2 = f1 - 3 dt/4 L(f0 - f1),  f3 = f2 + 2 dt/3 L(f0 - f1 + f2),
+//   f  = f3 - dt/4 L(f0 - f1 + f2 - f3),
+// f0 the collided state.  The stage and assembly kernels form A b + B (g + dt L g); a stage
+// f^s = f^{s-1} + c dt L(g) runs them with g the stage argument, B = c, A = 1 and
+// b = f^{s-1} - c g (both written by one combination pass).  Stage 1 (g = f0, c = 1/3) takes
+// b = 2/3 f0 where the kernel adds A b, and the whole-element kernel's first stage keeps f0
+// with weight 1 by itself.
+template <typename Real>
+cudaError_t enqueue_step_printed(selbm *h, bool apply_filter) {
+  KParams<Real> p = base_params<Real>(h);
+  Real *FA = (Real *)h->FA, *F0 = (Real *)h->F0, *F1 = (Real *)h->F2;
+  Real *F2 = (Real *)h->S1, *F3 = (Real *)h->S2, *GS = (Real *)h->SG, *BS = (Real *)h->SB;
+  const size_t nv = (size_t)h->Q * h->S.G;
+  const double third[4] = {2.0 / 3.0, 0, 0, 0};
+  cudaError_t e;
+  // stage 1 (collision and pending filter included): f1 = f0 + dt/3 L f0
+  if (h->use_split) {
+    p.stage = 1; p.A = Real(0); p.B = Real(1);
+    p.fin = FA; p.f0out = F0;
+    if (apply_filter && h->learned) {
+      if ((e = launch_split_prologue<Real>(h, PRO_LEARNED, p, learned_ptrs<Real>(h, true)))) return e;
+      if ((e = launch_drift_check(h->d_acc, h->d_flag, h->mass_bound, h->ke_bound, h->has_force ? 0 : 1, h->stream))) return e;
+      if ((e = launch_split_collide<Real>(h, 1, p))) return e;
+    } else {
+      e = apply_filter ? launch_split_prologue<Real>(h, PRO_FIXED, p, LearnedPtrs<Real>{}) : launch_split_collide<Real>(h, 0, p);
+      if (e) return e;
+    }
+    // b = 2/3 f0 (GS unused here), then A b + 1/3 (f0 + dt L f0)
+    if ((e = launch_combine<Real>(nv, F0, F0, F0, F0, 1, third, F0, 0.0, BS, GS, h->stream))) return e;
+    p.stage = 2; p.A = Real(1); p.B = Real(1.0 / 3.0); p.apply_filter = 0;
+    p.fin = F0; p.f0 = BS; p.fout = F1; p.f0out = nullptr;
+    if ((e = launch_split_stage<Real>(h, p))) return e;
+    if ((e = launch_dss<Real>(h->lat, p, h->stream))) return e;
+  } else {
+    if (apply_filter && h->learned) {
+      if ((e = enqueue_learned_filter<Real>(h, FA, FA, true))) return e;
+      apply_filter = false;
+    }
+    // the first stage of the whole-element kernel writes f0 + B dt L f0 at interior nodes
+    p.stage = 1; p.A = Real(0); p.B = Real(1.0 / 3.0);
+    p.apply_filter = apply_filter ? 1 : 0;
+    p.fin = FA; p.f0 = F0; p.fout = F1; p.f0out = F0;
+    if ((e = launch_stage_any<Real>(h, p))) return e;
+    // shared nodes: A b + B (f0 + ...) with b = 2/3 f0
+    if ((e = launch_combine<Real>(nv, F0, F0, F0, F0, 1, third, F0, 0.0, BS, GS, h->stream))) return e;
+    KParams<Real> q = p;
+    q.A = Real(1); q.fin = F0; q.f0 = BS;
+    if ((e = launch_dss<Real>(h->lat, q, h->stream))) return e;
+  }
+  // stages 2-4
+  const double cs[3] = {-0.75, 2.0 / 3.0, -0.25};
+  const double comb[3][4] = {{1, -1, 0, 0}, {1, -1, 1, 0}, {1, -1, 1, -1}};
+  Real *base[3] = {F1, F2, F3};
+  Real *outs[3] = {F2, F3, FA};
+  for (int s = 0; s < 3; ++s) {
+    if ((e = launch_combine<Real>(nv, F0, F1, F2, F3, s + 2, comb[s], base[s], cs[s], GS, BS, h->stream))) return e;
+    p.stage = 2; p.A = Real(1); p.B = Real(cs[s]); p.apply_filter = 0;
+    p.fin = GS; p.f0 = BS; p.fout = outs[s]; p.f0out = nullptr;
+    if (h->use_split) e = launch_split_stage<Real>(h, p);
+    else e = launch_stage_any<Real>(h, p);
+    if (e) return e;
+    if ((e = launch_dss<Real>(h->lat, p, h->stream))) return e;
+  }
+  return cudaSuccess;
+}
+
 // one time step: three stages, each = element kernel + assembly kernel
 template <typename Real>
 cudaError_t enqueue_step(selbm *h, bool apply_filter) {
@@ -367,6 +437,7 @@ cudaError_t enqueue_step(selbm *h, bool apply_filter) {
     cudaError_t e = launch_force_amp<Real>(h->d_ft, (Real *)h->d_famp, h->dt, h->f_period, h->f_tend, h->stream);
     if (e != cudaSuccess) return e;
   }
+  if (h->scheme == 1) return enqueue_step_printed<Real>(h, apply_filter);
   KParams<Real> p = base_params<Real>(h);
   if (h->use_split) return enqueue_step_split<Real>(h, apply_filter);
   Real *FA = (Real *)h->FA, *F0 = (Real *)h->F0, *F2 = (Real *)h->F2;
@@ -720,6 +791,23 @@ int selbm_set_body_force(selbm_t *h, const double g[3]) {
   if (!h || !g) return SELBM_ERR_ARG;
   for (int k = 0; k < 3; ++k) h->P.body_accel[k] = g[k];
   h->has_force = g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0 || h->field_on;
+  h->invalidate_graph();
+  return SELBM_OK;
+}
+
+int selbm_set_time_scheme(selbm_t *h, int scheme) {
+  if (!h) return SELBM_ERR_ARG;
+  if (scheme != 0 && scheme != 1) return h->fail(SELBM_ERR_ARG, "time scheme must be 0 or 1");
+  if (scheme == 1 && !h->S1) {
+    const size_t bytes = (size_t)h->Q * h->S.G * h->rsz;
+    void **bufs[4] = {&h->S1, &h->S2, &h->SG, &h->SB};
+    for (void **b : bufs) {
+      cudaError_t e = cudaMalloc(b, bytes);
+      if (e != cudaSuccess) return h->cuda_fail(e, "time scheme buffers");
+      h->allocs.push_back(*b);
+    }
+  }
+  h->scheme = scheme;
   h->invalidate_graph();
   return SELBM_OK;
 }

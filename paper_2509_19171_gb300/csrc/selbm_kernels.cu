@@ -625,6 +625,27 @@ cudaError_t launch_init(int lat, const double *rho, const double *u, const int32
   return cudaGetLastError();
 }
 
+template <typename Real>
+__global__ void combine_kernel(size_t n, const Real *f0, const Real *f1, const Real *f2, const Real *f3, int m,
+                               Real c0, Real c1, Real c2, Real c3, const Real *base, Real cb, Real *g, Real *b) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    Real v = c0 * f0[i];
+    if (m > 1) v += c1 * f1[i];
+    if (m > 2) v += c2 * f2[i];
+    if (m > 3) v += c3 * f3[i];
+    g[i] = v;
+    b[i] = base[i] - cb * v;
+  }
+}
+template <typename Real>
+cudaError_t launch_combine(size_t n, const Real *f0, const Real *f1, const Real *f2, const Real *f3, int m,
+                           const double c[4], const Real *base, double cb, Real *g, Real *b, cudaStream_t s) {
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  combine_kernel<Real><<<blocks, 256, 0, s>>>(n, f0, f1, f2, f3, m, (Real)c[0], (Real)c[1], (Real)c[2], (Real)c[3],
+                                              base, (Real)cb, g, b);
+  return cudaGetLastError();
+}
+
 // per-node acceleration field on unique nodes from the first local copy of each node
 template <typename Real>
 __global__ void force_field_kernel(const double *S, const int32_t *first, int G, int dim, Real *fS) {
@@ -682,6 +703,8 @@ cudaError_t launch_diag(int lat, const Real *buf, const double *mass, int G, dou
   template cudaError_t launch_init<Real>(int, const double *, const double *, const int32_t *, int, double, double,      \
                                          const double[3], int, const Real *, double, Real *, cudaStream_t);              \
   template cudaError_t launch_force_field<Real>(const double *, const int32_t *, int, int, Real *, cudaStream_t);         \
+  template cudaError_t launch_combine<Real>(size_t, const Real *, const Real *, const Real *, const Real *, int,         \
+                                            const double[4], const Real *, double, Real *, Real *, cudaStream_t);        \
   template cudaError_t launch_force_amp<Real>(double *, Real *, double, double, double, cudaStream_t);                    \
   template cudaError_t launch_set_state<Real>(int, const double *, const int32_t *, int, size_t, double, Real *, cudaStream_t); \
   template cudaError_t launch_get_state<Real>(int, const Real *, const int32_t *, int, size_t, double, double *, cudaStream_t); \

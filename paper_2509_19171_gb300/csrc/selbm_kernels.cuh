@@ -78,6 +78,12 @@ template <typename Real>
 cudaError_t launch_init(int lat, const double *rho, const double *u, const int32_t *first, int G, double rho0,
                         double half_dt, const double g[3], int has_force, const Real *fS, double amp, Real *out,
                         cudaStream_t s);
+// g = sum_{i < m} c_i f_i and b = base - cb g over n values (m <= 4): the argument of a stage
+// of the printed four-stage scheme and the base that makes A b + B (g + dt L g) with A = 1,
+// B = cb equal to base + cb dt L g
+template <typename Real>
+cudaError_t launch_combine(size_t n, const Real *f0, const Real *f1, const Real *f2, const Real *f3, int m,
+                           const double c[4], const Real *base, double cb, Real *g, Real *b, cudaStream_t s);
 // per-node acceleration field: fS[k][g] = S[first[g]][k] (k < dim), 0 for k >= dim
 template <typename Real>
 cudaError_t launch_force_field(const double *S, const int32_t *first, int G, int dim, Real *fS, cudaStream_t s);
