@@ -68,3 +68,14 @@ def test_printed_scheme_step_conserves_mass_with_force():
         f = o.step(f)
     m1, _, _ = o.integrals(f)
     assert abs(m1 - m0) < 1e-13 * m0
+
+
+def test_printed_stages_cancel_a_constant_source():
+    """A uniform state under a uniform F*: every application of L returns F* (nothing to
+    advect), and the printed stage weights 1/3 - 3/4 + 2/3 - 1/4 sum to zero, so the printed
+    stages leave the state unchanged, while the Shu-Osher stages add dt F*."""
+    o = periodic_oracle(N=4)
+    f0 = np.tile(o.t[:, None], (1, o.G))
+    Fs = np.tile((o.t * (o.e.astype(float) @ np.array([3e-4, -2e-4])) * 3.0)[:, None], (1, o.G))
+    assert np.abs(o.rk_printed(f0, Fs) - f0).max() < 1e-15
+    assert np.abs(o.ssprk3(f0, Fs) - (f0 + o.dt * Fs)).max() < 1e-15
