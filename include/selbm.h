@@ -158,9 +158,14 @@ int selbm_set_filter(selbm_t *h, const selbm_filter *filter);
  *   f  = f3 - dt/4 L(f0 - f1 + f2 - f3),
  * f0 the collided state, L applied to each combination as a whole (its force and
  * wall-velocity terms once per application); for a linear L (no force, walls at rest) this is
- * the fourth-order Taylor polynomial of exp(dt L).  The first call with 1 allocates three
- * more state arrays (3 Q G reals), freed by selbm_destroy.  Takes effect from the next step.
- * Errors: SELBM_ERR_ARG (h NULL, scheme not 0 or 1), SELBM_ERR_CUDA (allocation failure).
+ * the fourth-order Taylor polynomial of exp(dt L).  Taken literally the four applications
+ * weight a source term of L by 1/3 - 3/4 + 2/3 - 1/4 = 0.  2: the printed stages with L's
+ * source terms (F*, moving-wall velocity) kept only for the arguments whose weights sum to
+ * one (f0 and f0 - f1 + f2) and dropped for the differences (f0 - f1, f0 - f1 + f2 - f3):
+ * fourth order in time for an affine L, steady states of L kept exactly.  The first call
+ * with 1 or 2 allocates four more state arrays (4 Q G reals), freed by selbm_destroy.  Takes
+ * effect from the next step.  Errors: SELBM_ERR_ARG (h NULL, scheme not 0, 1 or 2),
+ * SELBM_ERR_CUDA (allocation failure).
  */
 int selbm_set_time_scheme(selbm_t *h, int scheme);
 /* Replace the body acceleration g (F = rho g). */

@@ -67,11 +67,14 @@ class OracleSELBM:
         self.g = g
         self.fS = None                                           # extra per-node acceleration field
         self.time = 0.0
-        self.scheme = 0                                          # 0 Shu-Osher SSPRK3, 1 printed stages
+        self.scheme = 0                                # 0 Shu-Osher SSPRK3, 1 printed stages, 2 weighted
 
     def set_time_scheme(self, scheme):
         """0: the Shu-Osher SSPRK3 that the text names; 1: the four stages as printed in
-        Sec. 2.2.2, with L applied to each stage combination as a whole."""
+        Sec. 2.2.2, with L applied to each stage combination as a whole; 2: the printed stages
+        with L's source terms (F*, moving walls) weighted by the combination's weight sum, i.e.
+        kept for the state arguments f0 and f0 - f1 + f2 and dropped for the differences
+        f0 - f1 and f0 - f1 + f2 - f3."""
         self.scheme = int(scheme)
 
     def set_force_field(self, S, period, t_end):
@@ -135,7 +138,7 @@ class OracleSELBM:
         return fstar, Fstar
 
     # ------------------------------------------------------------- streaming
-    def element_contribution(self, f):
+    def element_contribution(self, f, wall_source=True):
         """Weighted element contribution c[Q, E, Np] of -C f + R (n.j) (Eqs. advection2, entire).
 
         Interior:  c = -wJ sum_l (sum_k e_k dr_l/dx_k) (D_l f)        (C = phi^T e G D* phi)
@@ -158,13 +161,15 @@ class OracleSELBM:
             for a in range(self.Q):
                 b = self.opp[a]
                 inc = ne[:, a] < 0.0
-                jump = fl[a, el, nodes] - fl[b, el, nodes] - 2.0 * self.t[a] * self.rho0 * (ef[a] @ ub) / CS2
+                jump = fl[a, el, nodes] - fl[b, el, nodes]
+                if wall_source:
+                    jump = jump - 2.0 * self.t[a] * self.rho0 * (ef[a] @ ub) / CS2
                 c[a, el, nodes] += np.where(inc, wsJs * ne[:, a] * jump, 0.0)
         return c
 
-    def rhs(self, f, Fstar):
+    def rhs(self, f, Fstar, wall_source=True):
         """L(f) = M^{-1} assemble(c) + F* on unique nodes (continuous Galerkin)."""
-        c = self.element_contribution(f)
+        c = self.element_contribution(f, wall_source)
         R = np.zeros((self.Q, self.G))
         for a in range(self.Q):
             np.add.at(R[a], self.glo.ravel(), c[a].ravel())       # ascending copy order
@@ -177,18 +182,25 @@ class OracleSELBM:
         f2 = 0.75 * f0 + 0.25 * (f1 + dt * self.rhs(f1, Fstar))
         return f0 / 3.0 + 2.0 / 3.0 * (f2 + dt * self.rhs(f2, Fstar))
 
-    def rk_printed(self, f0, Fstar):
+    def rk_printed(self, f0, Fstar, weighted=False):
         """The four stages as printed (Sec. 2.2.2):
         f1 = f0 + dt/3 L f0,  f2 = f1 - 3dt/4 L(f0 - f1),  f3 = f2 + 2dt/3 L(f0 - f1 + f2),
-        f = f3 - dt/4 L(f0 - f1 + f2 - f3)."""
+        f = f3 - dt/4 L(f0 - f1 + f2 - f3).
+        weighted: the arguments f0 - f1 and f0 - f1 + f2 - f3 (weights summing to zero) take
+        L without its source terms (F*, wall velocity)."""
         dt = self.dt
+
+        def Ld(g):
+            return self.rhs(g, 0.0 * Fstar, wall_source=False) if weighted else self.rhs(g, Fstar)
         f1 = f0 + dt / 3.0 * self.rhs(f0, Fstar)
-        f2 = f1 - 0.75 * dt * self.rhs(f0 - f1, Fstar)
+        f2 = f1 - 0.75 * dt * Ld(f0 - f1)
         f3 = f2 + 2.0 / 3.0 * dt * self.rhs(f0 - f1 + f2, Fstar)
-        return f3 - 0.25 * dt * self.rhs(f0 - f1 + f2 - f3, Fstar)
+        return f3 - 0.25 * dt * Ld(f0 - f1 + f2 - f3)
 
     def stream(self, f0, Fstar):
-        return self.ssprk3(f0, Fstar) if self.scheme == 0 else self.rk_printed(f0, Fstar)
+        if self.scheme == 0:
+            return self.ssprk3(f0, Fstar)
+        return self.rk_printed(f0, Fstar, weighted=self.scheme == 2)
 
     # ----------------------------------------------------------------- filter
     def assemble_average(self, fl):

@@ -283,7 +283,8 @@ class SELBM:
         self._check(self.lib.selbm_set_force_field(self.h, _dptr(a), float(period), float(t_end)))
 
     def set_time_scheme(self, scheme):
-        """0: Shu-Osher SSPRK3 (default); 1: the four stages as printed (selbm_set_time_scheme)."""
+        """0: Shu-Osher SSPRK3 (default); 1: the four stages as printed; 2: the printed stages with
+        the source terms kept for state arguments only (selbm_set_time_scheme)."""
         self._check(self.lib.selbm_set_time_scheme(self.h, int(scheme)))
 
     def clear_force_field(self):

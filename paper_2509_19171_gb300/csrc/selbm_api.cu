@@ -87,6 +87,7 @@ struct selbm {
   void *FA = nullptr, *F0 = nullptr, *F2 = nullptr, *T = nullptr, *RHO = nullptr, *BUF = nullptr;
   void *d_el_drdx = nullptr, *d_el_J = nullptr, *d_drdx = nullptr, *d_wJ = nullptr, *d_gllw = nullptr;
   void *d_D = nullptr, *d_F = nullptr, *d_wall_u = nullptr, *d_walls = nullptr, *d_minv = nullptr;
+  void *d_wall_u0 = nullptr;   // walls at rest (the source-free operator of time scheme 2)
   int32_t *d_l2g = nullptr, *d_bslot = nullptr, *d_bnode_g = nullptr, *d_bnode_off = nullptr, *d_bnode_slot = nullptr;
   int32_t *d_wall_off = nullptr, *d_first = nullptr;
   uint8_t *d_owner = nullptr;
@@ -182,6 +183,8 @@ cudaError_t upload_real(selbm *h) {
   std::vector<double> wu = S.wall_u;
   if (wu.empty()) wu.assign(3, 0.0);
   if ((e = upload(&p, cast_vec<Real>(wu)))) return e; h->d_wall_u = p; h->allocs.push_back(p);
+  std::vector<double> wz(wu.size(), 0.0);
+  if ((e = upload(&p, cast_vec<Real>(wz)))) return e; h->d_wall_u0 = p; h->allocs.push_back(p);
   std::vector<double> minv(S.Gb);
   for (int u = 0; u < S.Gb; ++u) minv[u] = 1.0 / S.mass[S.bnode_g[u]];
   if ((e = upload(&p, cast_vec<Real>(minv)))) return e; h->d_minv = p; h->allocs.push_back(p);
@@ -411,7 +414,9 @@ cudaError_t enqueue_step_printed(selbm *h, bool apply_filter) {
     q.A = Real(1); q.fin = F0; q.f0 = BS;
     if ((e = launch_dss<Real>(h->lat, q, h->stream))) return e;
   }
-  // stages 2-4
+  // stages 2-4; with scheme 2 the difference arguments (stages 2 and 4) take L without its
+  // source terms: no F*, walls at rest
+  const KParams<Real> full = p;
   const double cs[3] = {-0.75, 2.0 / 3.0, -0.25};
   const double comb[3][4] = {{1, -1, 0, 0}, {1, -1, 1, 0}, {1, -1, 1, -1}};
   Real *base[3] = {F1, F2, F3};
@@ -420,6 +425,10 @@ cudaError_t enqueue_step_printed(selbm *h, bool apply_filter) {
     if ((e = launch_combine<Real>(nv, F0, F1, F2, F3, s + 2, comb[s], base[s], cs[s], GS, BS, h->stream))) return e;
     p.stage = 2; p.A = Real(1); p.B = Real(cs[s]); p.apply_filter = 0;
     p.fin = GS; p.f0 = BS; p.fout = outs[s]; p.f0out = nullptr;
+    const bool diff = h->scheme == 2 && s != 1;
+    p.has_force = diff ? 0 : full.has_force;
+    p.fS = diff ? nullptr : full.fS;
+    p.wall_u = diff ? (const Real *)h->d_wall_u0 : full.wall_u;
     if (h->use_split) e = launch_split_stage<Real>(h, p);
     else e = launch_stage_any<Real>(h, p);
     if (e) return e;
@@ -437,7 +446,7 @@ cudaError_t enqueue_step(selbm *h, bool apply_filter) {
     cudaError_t e = launch_force_amp<Real>(h->d_ft, (Real *)h->d_famp, h->dt, h->f_period, h->f_tend, h->stream);
     if (e != cudaSuccess) return e;
   }
-  if (h->scheme == 1) return enqueue_step_printed<Real>(h, apply_filter);
+  if (h->scheme != 0) return enqueue_step_printed<Real>(h, apply_filter);
   KParams<Real> p = base_params<Real>(h);
   if (h->use_split) return enqueue_step_split<Real>(h, apply_filter);
   Real *FA = (Real *)h->FA, *F0 = (Real *)h->F0, *F2 = (Real *)h->F2;
@@ -797,8 +806,8 @@ int selbm_set_body_force(selbm_t *h, const double g[3]) {
 
 int selbm_set_time_scheme(selbm_t *h, int scheme) {
   if (!h) return SELBM_ERR_ARG;
-  if (scheme != 0 && scheme != 1) return h->fail(SELBM_ERR_ARG, "time scheme must be 0 or 1");
-  if (scheme == 1 && !h->S1) {
+  if (scheme < 0 || scheme > 2) return h->fail(SELBM_ERR_ARG, "time scheme must be 0, 1 or 2");
+  if (scheme != 0 && !h->S1) {
     const size_t bytes = (size_t)h->Q * h->S.G * h->rsz;
     void **bufs[4] = {&h->S1, &h->S2, &h->SG, &h->SB};
     for (void **b : bufs) {

@@ -79,3 +79,39 @@ def test_printed_stages_cancel_a_constant_source():
     Fs = np.tile((o.t * (o.e.astype(float) @ np.array([3e-4, -2e-4])) * 3.0)[:, None], (1, o.G))
     assert np.abs(o.rk_printed(f0, Fs) - f0).max() < 1e-15
     assert np.abs(o.ssprk3(f0, Fs) - (f0 + o.dt * Fs)).max() < 1e-15
+
+
+def test_weighted_reading_fourth_order_with_source_and_steady_states():
+    """Time scheme 2: the printed stages with L's source terms kept for the state arguments
+    (f0, f0 - f1 + f2) and dropped for the differences.  Without sources it is the printed
+    scheme; with a constant source it is fourth order in time; a steady state of L with a
+    moving wall and a force is kept exactly (the literal reading moves it)."""
+    o = periodic_oracle(N=8)
+    rng = np.random.default_rng(4)
+    f = rng.standard_normal((o.Q, o.G))
+    z = np.zeros_like(f)
+    assert np.array_equal(o.rk_printed(f, z, weighted=True), o.rk_printed(f, z))
+    f0 = np.tile(np.sin(o.Xg[:, 0] + 0.1)[None] * np.cos(o.Xg[:, 1])[None], (o.Q, 1))
+    b = 0.3 * np.tile((np.cos(o.Xg[:, 1]) + 0.2)[None], (o.Q, 1)) * o.t[:, None]
+    T = 0.4
+
+    def run(n):
+        dt_save = o.dt
+        o.dt = T / n
+        g = f0.copy()
+        for _ in range(n):
+            g = o.rk_printed(g, b, weighted=True)
+        o.dt = dt_save
+        return g
+
+    ref = run(256)
+    errs = [np.abs(run(n) - ref).max() for n in (8, 16, 32)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(3.7 < r < 4.3 for r in rates), rates
+    # steady state of L on a box with a moving lid
+    c = W.couette_case()
+    q = OracleSELBM(c.mesh, c.lattice, c.order, c.nu, cfl=c.cfl)
+    fs = q.initial_state_from(c.init) + 1e-3 * q.t[:, None] * rng.standard_normal((q.Q, q.G))
+    Fs = -q.rhs(fs, np.zeros_like(fs))
+    assert np.array_equal(q.rk_printed(fs, Fs, weighted=True), fs)
+    assert np.abs(q.rk_printed(fs, Fs) - fs).max() > 1e-6 * np.abs(fs).max()
