@@ -807,12 +807,18 @@ int selbm_set_body_force(selbm_t *h, const double g[3]) {
 int selbm_set_time_scheme(selbm_t *h, int scheme) {
   if (!h) return SELBM_ERR_ARG;
   if (scheme < 0 || scheme > 2) return h->fail(SELBM_ERR_ARG, "time scheme must be 0, 1 or 2");
-  if (scheme != 0 && !h->S1) {
+  if (scheme != 0) {
+    // allocate whichever stage buffers are still missing (a failed call leaves the rest for
+    // the next one)
     const size_t bytes = (size_t)h->Q * h->S.G * h->rsz;
     void **bufs[4] = {&h->S1, &h->S2, &h->SG, &h->SB};
     for (void **b : bufs) {
+      if (*b) continue;
       cudaError_t e = cudaMalloc(b, bytes);
-      if (e != cudaSuccess) return h->cuda_fail(e, "time scheme buffers");
+      if (e != cudaSuccess) {
+        *b = nullptr;
+        return h->cuda_fail(e, "time scheme buffers");
+      }
       h->allocs.push_back(*b);
     }
   }
