@@ -839,13 +839,16 @@ int selbm_set_force_field(selbm_t *h, const double *S, double period, double t_e
   if (std::isnan(period) || std::isnan(t_end)) return h->fail(SELBM_ERR_ARG, "force field period / t_end is NaN");
   const size_t G = (size_t)h->S.G, nl = h->nloc(), d = h->S.dim;
   cudaError_t e = cudaSuccess;
-  if (!h->d_fS) {
-    if ((e = cudaMalloc(&h->d_fS, 3 * G * h->rsz)) != cudaSuccess) return h->cuda_fail(e, "force field alloc");
-    h->allocs.push_back(h->d_fS);
-    if ((e = cudaMalloc(&h->d_famp, 16)) != cudaSuccess) return h->cuda_fail(e, "force field alloc");
-    h->allocs.push_back(h->d_famp);
-    if ((e = cudaMalloc((void **)&h->d_ft, sizeof(double))) != cudaSuccess) return h->cuda_fail(e, "force field alloc");
-    h->allocs.push_back(h->d_ft);
+  // allocate whichever of the field buffers are still missing
+  struct { void **ptr; size_t bytes; } need[3] = {{&h->d_fS, 3 * G * h->rsz}, {&h->d_famp, 16},
+                                                  {(void **)&h->d_ft, sizeof(double)}};
+  for (auto &b : need) {
+    if (*b.ptr) continue;
+    if ((e = cudaMalloc(b.ptr, b.bytes)) != cudaSuccess) {
+      *b.ptr = nullptr;
+      return h->cuda_fail(e, "force field alloc");
+    }
+    h->allocs.push_back(*b.ptr);
   }
   int rc = ensure_io(h, nl * d * sizeof(double));
   if (rc) return rc;
