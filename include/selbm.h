@@ -139,7 +139,9 @@ int selbm_get_state(selbm_t *h, double *f, int on_device);
 /*
  * Advance nsteps time steps (Sec. 2, summary list): BGK collision with F**,
  * three Shu-Osher SSPRK3 stages of the weak advection with F* and the flux
- * bounce-back wall flux, assembly of shared nodes, explicit filter.
+ * bounce-back wall flux (or the four printed stages, see selbm_set_time_scheme),
+ * assembly of shared nodes, explicit filter.  Each step is launched as a captured
+ * CUDA graph after one eager step of its kind.
  * Asynchronous: enqueues the work and returns.  Errors: SELBM_ERR_STATE
  * (not initialised), SELBM_ERR_CUDA (launch failure).
  */
