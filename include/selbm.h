@@ -151,6 +151,17 @@ int selbm_step(selbm_t *h, int64_t nsteps);
  * at every local node: rho [E][Np], u [E][Np][dim]. */
 int selbm_moments(selbm_t *h, double *rho, double *u, int on_device);
 
+/*
+ * Non-equilibrium second moment at every local node (Sec. 3.3, the stress recovered from the
+ * higher moments of the distribution): Pi_ij = tau / (tau + 1/2) sum_a e_ai e_aj (f_bar_a -
+ * f_bar_a^eq), f_bar^eq = f^eq - dt/2 F** at the node's (rho, u) and force; the factor turns
+ * the non-equilibrium part of f_bar into that of f.  To leading order -Pi is the viscous
+ * stress rho nu (d_i u_j + d_j u_i); in planar shear flow -Pi_xx carries the normal stress
+ * -2 mu lambda (u')^2.  Read from the filtered state, as selbm_moments.  pi [E][Np][dim][dim],
+ * host or device (on_device = 1).  Errors: SELBM_ERR_ARG, SELBM_ERR_STATE, SELBM_ERR_CUDA.
+ */
+int selbm_stress(selbm_t *h, double *pi, int on_device);
+
 /* Replace the filter (Sec. 2.4); takes effect from the next step. */
 int selbm_set_filter(selbm_t *h, const selbm_filter *filter);
 /*

@@ -327,6 +327,19 @@ class OracleSELBM:
         mean = np.divide(su, mass, out=np.zeros(nbins), where=mass > 0)
         return mean, mass
 
+    def stress(self, f):
+        """Non-equilibrium second moment on unique nodes (Sec. 3.3: the stress recovered from the
+        higher moments of the distribution), Pi_ij = tau / (tau + 1/2) sum_a e_ai e_aj (f_bar_a -
+        f_bar_a^eq), with f_bar^eq = f^eq - dt/2 F** the collision's target at the node's (rho, u);
+        the factor turns the non-equilibrium part of f_bar into that of f.  To leading order
+        -Pi_ij = rho nu (d_i u_j + d_j u_i), the viscous stress.  Returns [G, d, d]."""
+        rho, u = self.moments(f)
+        F = rho[:, None] * self.accel()
+        _, Fss = force_split(self.e, self.t, u, F)
+        neq = f - (equilibrium(self.e, self.t, rho, u) - 0.5 * self.dt * Fss)
+        ef = self.e.astype(float)
+        return np.einsum("ai,aj,an->nij", ef, ef, neq) * (self.tau / (self.tau + 0.5))
+
     def integrals(self, f):
         """Quadrature integrals: mass sum M rho, momentum sum M rho u, KE = sum M rho0 |u|^2 / 2."""
         rho, u = self.moments(f)

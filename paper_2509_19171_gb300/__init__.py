@@ -26,7 +26,7 @@ ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_MESH", -3: "ERR_CUDA", -4: "ERR_NONFI
 # functions declared in include/selbm.h (checked by the ABI test)
 EXPORTS = ["selbm_create", "selbm_destroy", "selbm_last_error", "selbm_info", "selbm_lattice_table",
            "selbm_node_coords", "selbm_init", "selbm_set_state", "selbm_get_state", "selbm_step",
-           "selbm_moments", "selbm_set_filter", "selbm_set_body_force", "selbm_set_force_field", "selbm_set_time_scheme",
+           "selbm_moments", "selbm_stress", "selbm_set_filter", "selbm_set_body_force", "selbm_set_force_field", "selbm_set_time_scheme",
            "selbm_diagnostics", "selbm_sync",
            "selbm_wall_stress", "selbm_radial_profile",
            "selbm_mesh_check", "selbm_timers", "selbm_timers_read", "selbm_set_learned_filter",
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
     lib.selbm_get_state.argtypes = [P, P, I]
     lib.selbm_step.argtypes = [P, I64]
     lib.selbm_moments.argtypes = [P, P, P, I]
+    lib.selbm_stress.argtypes = [P, P, I]
     lib.selbm_set_filter.argtypes = [P, C.POINTER(FilterC)]
     lib.selbm_set_body_force.argtypes = [P, D]
     lib.selbm_set_force_field.argtypes = [P, P, C.c_double, C.c_double]
@@ -264,6 +265,12 @@ class SELBM:
         pu, _ = _ptr_of(u)
         self._check(self.lib.selbm_moments(self.h, pr, pu, dev))
         return rho, u
+
+    def stress(self):
+        """Non-equilibrium second moment Pi [E, Np, dim, dim] (selbm_stress)."""
+        pi = np.zeros((self.E, self.Np, self.dim, self.dim))
+        self._check(self.lib.selbm_stress(self.h, _dptr(pi), 0))
+        return pi
 
     def set_filter(self, f):
         fs = filter_struct(f)

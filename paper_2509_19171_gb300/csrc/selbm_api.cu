@@ -782,6 +782,37 @@ int selbm_moments(selbm_t *h, double *rho, double *u, int on_device) {
   return SELBM_OK;
 }
 
+int selbm_stress(selbm_t *h, double *pi, int on_device) {
+  if (!h || !pi) return SELBM_ERR_ARG;
+  if (!h->initialized) return h->fail(SELBM_ERR_STATE, "state not initialised");
+  int rc = finalize(h);
+  if (rc) return rc;
+  const size_t nl = h->nloc(), d = h->S.dim, n = nl * d * d;
+  double *dp = pi;
+  if (!on_device) {
+    if ((rc = ensure_io(h, n * 8))) return rc;
+    dp = h->d_io;
+  }
+  // the acceleration field's time factor at the read-back time
+  const double t = h->time;
+  const double amp = !h->field_on || !(t < h->f_tend)
+                         ? 0.0
+                         : (h->f_period > 0.0 ? std::sin(2.0 * 3.14159265358979323846 * t / h->f_period) : 1.0);
+  const double factor = h->tau / (h->tau + 0.5);
+  const double *g = h->P.body_accel;
+  cudaError_t e = h->prec == SELBM_FP64
+                      ? launch_stress<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, 0.5 * h->dt,
+                                              factor, g, h->has_force, h->field_on ? (const double *)h->d_fS : nullptr,
+                                              amp, dp, h->stream)
+                      : launch_stress<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, 0.5 * h->dt,
+                                             factor, g, h->has_force, h->field_on ? (const float *)h->d_fS : nullptr,
+                                             amp, dp, h->stream);
+  if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(pi, dp, n * 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "stress");
+  return SELBM_OK;
+}
+
 int selbm_set_filter(selbm_t *h, const selbm_filter *f) {
   if (!h || !f) return SELBM_ERR_ARG;
   if (h->filter_pending && (h->filter_on || h->learned)) {

@@ -484,6 +484,48 @@ __global__ void moments_kernel(const Real *buf, const int32_t *l2g, int G, size_
   }
 }
 
+// non-equilibrium second moment at every local node, Pi_ij = factor sum_a e_ai e_aj (f_a - f_a^eq
+// + dt/2 F**_a), factor = tau / (tau + 1/2); the buffer holds deviations f - t rho0; acceleration
+// g + amp S_g (amp the field's time factor at the read-back time)
+template <typename Real, int LAT>
+__global__ void stress_kernel(const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double half_dt,
+                              double factor, double g0, double g1, double g2, int has_force, const Real *fS, double amp,
+                              double *out) {
+  constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nloc; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t g = l2g[q];
+    double d = 0, j[3] = {0, 0, 0};
+    for (int a = 0; a < Q; ++a) {
+      const double v = (double)buf[(size_t)a * G + g];
+      d += v;
+      for (int k = 0; k < DIM; ++k) j[k] += c_e[LAT][a][k] * v;
+    }
+    const double r = rho0 + d;
+    double u[3] = {0, 0, 0}, F[3] = {0, 0, 0}, acc[3] = {g0, g1, g2}, uu = 0, uF = 0;
+    if (fS)
+      for (int k = 0; k < 3; ++k) acc[k] += amp * (double)fS[(size_t)k * G + g];
+    for (int k = 0; k < DIM; ++k) {
+      u[k] = j[k] / r;
+      uu += u[k] * u[k];
+      F[k] = has_force ? r * acc[k] : 0.0;
+      uF += u[k] * F[k];
+    }
+    double pi[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a = 0; a < Q; ++a) {
+      double eu = 0, eF = 0;
+      for (int k = 0; k < DIM; ++k) { eu += c_e[LAT][a][k] * u[k]; eF += c_e[LAT][a][k] * F[k]; }
+      const double t = c_td[LAT][a];
+      // f - f^eq with f = buf + t rho0 and f^eq = t rho (1 + 3 eu + 4.5 eu^2 - 1.5 uu), rho = rho0 + d
+      const double neq = (double)buf[(size_t)a * G + g] - t * (d + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu)) +
+                         half_dt * t * (9.0 * eu * eF - 3.0 * uF);
+      for (int i = 0; i < DIM; ++i)
+        for (int k = 0; k < DIM; ++k) pi[i][k] += (double)(c_e[LAT][a][i] * c_e[LAT][a][k]) * neq;
+    }
+    for (int i = 0; i < DIM; ++i)
+      for (int k = 0; k < DIM; ++k) out[(q * DIM + i) * DIM + k] = factor * pi[i][k];
+  }
+}
+
 // per-block partial sums: mass, momentum[3], KE, non-finite count (deterministic two-pass)
 template <typename Real, int LAT>
 __global__ void diag_partial_kernel(const Real *buf, const double *mass, int G, double rho0, double *partial) {
@@ -691,6 +733,14 @@ cudaError_t launch_moments(int lat, const Real *buf, const int32_t *l2g, int G, 
   SELBM_LAT_SWITCH(lat, (moments_kernel<Real, L><<<grid_for(nloc, 256), 256, 0, s>>>(buf, l2g, G, nloc, rho0, rho, u)));
   return cudaGetLastError();
 }
+template <typename Real>
+cudaError_t launch_stress(int lat, const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double half_dt,
+                          double factor, const double g[3], int has_force, const Real *fS, double amp, double *out,
+                          cudaStream_t s) {
+  SELBM_LAT_SWITCH(lat, (stress_kernel<Real, L><<<grid_for(nloc, 256), 256, 0, s>>>(
+                             buf, l2g, G, nloc, rho0, half_dt, factor, g[0], g[1], g[2], has_force, fS, amp, out)));
+  return cudaGetLastError();
+}
 int diag_blocks() { return 152 * 4; }
 template <typename Real>
 cudaError_t launch_diag(int lat, const Real *buf, const double *mass, int G, double rho0, double *partial, double *out, cudaStream_t s) {
@@ -706,6 +756,8 @@ cudaError_t launch_diag(int lat, const Real *buf, const double *mass, int G, dou
   template cudaError_t launch_combine<Real>(size_t, const Real *, const Real *, const Real *, const Real *, int,         \
                                             const double[4], const Real *, double, Real *, Real *, cudaStream_t);        \
   template cudaError_t launch_force_amp<Real>(double *, Real *, double, double, double, cudaStream_t);                    \
+  template cudaError_t launch_stress<Real>(int, const Real *, const int32_t *, int, size_t, double, double, double,        \
+                                           const double[3], int, const Real *, double, double *, cudaStream_t);          \
   template cudaError_t launch_set_state<Real>(int, const double *, const int32_t *, int, size_t, double, Real *, cudaStream_t); \
   template cudaError_t launch_get_state<Real>(int, const Real *, const int32_t *, int, size_t, double, double *, cudaStream_t); \
   template cudaError_t launch_moments<Real>(int, const Real *, const int32_t *, int, size_t, double, double *, double *, cudaStream_t); \

@@ -87,6 +87,11 @@ cudaError_t launch_combine(size_t n, const Real *f0, const Real *f1, const Real 
 // per-node acceleration field: fS[k][g] = S[first[g]][k] (k < dim), 0 for k >= dim
 template <typename Real>
 cudaError_t launch_force_field(const double *S, const int32_t *first, int G, int dim, Real *fS, cudaStream_t s);
+// non-equilibrium second moment at every local node, out [nloc][dim][dim]
+template <typename Real>
+cudaError_t launch_stress(int lat, const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double half_dt,
+                          double factor, const double g[3], int has_force, const Real *fS, double amp, double *out,
+                          cudaStream_t s);
 // time factor of the field for the step starting at ft[0]; advances ft[0] by dt
 template <typename Real>
 cudaError_t launch_force_amp(double *ft, Real *amp, double dt, double period, double t_end, cudaStream_t s);

@@ -1,11 +1,12 @@
 """Numerical slip of the flux bounce-back wall in planar Poiseuille flow (Sec. 3.3): the
 dimensionless wall velocity u_slip* = u_x(y = 0) / u_max at steady state for a sweep of the
-relaxation time tau = lambda / dt and of the time step dt (through the CFL number).
+relaxation time tau = lambda / dt and of the time step dt (through the CFL number), and the wall
+normal stress T_xx = -Pi_xx (selbm_stress) against -2 mu lambda (u')^2.
 
 Unit square, 4 x 4 quads, N = 8, D2Q9, periodic in x, walls at y = 0 and 1, driven by the
 body force G = 8 nu u_max with u_max = 0.1 / 3 (Ma = 0.1 / sqrt(3)), nu = tau dt cs^2.  Each
 case starts on the analytic parabola and runs until u_slip* changes by less than a tolerance
-between two checks.  Every number comes from the library (steps, selbm_moments); this module
+between two checks.  Every number comes from the library (steps, selbm_moments, selbm_stress); this module
 schedules the runs and reads the wall nodes.
 
 python -m paper_2509_19171_gb300.poiseuille_slip --out slip.json
@@ -51,8 +52,15 @@ def run(taus=(0.1, 0.2, 0.3, 0.4), cfls=(0.5, 0.25, 0.125), ne=4, order=8, check
                 if prev is not None and abs(slip - prev) < tol:
                     break
                 prev = slip
+            # wall normal stress T_xx = -Pi_xx against -2 mu lambda (u')^2 with the analytic u'
+            rho, _ = s.moments()
+            pi = s.stress()
+            txx = -pi.reshape(-1, 2, 2)[wall, 0, 0]
+            lam = tau * dt
+            expect = -2.0 * rho.reshape(-1)[wall] * nu * lam * (G / (2.0 * nu)) ** 2
             out.append({"cfl": cfl, "tau": tau, "dt": dt, "nu": nu, "steps": steps, "u_slip_star": slip,
                         "profile_err_over_umax": err, "converged": prev is not None and abs(slip - prev) < tol,
+                        "txx_wall_over_burnett": float(np.mean(txx / expect)),
                         "wall_s": round(time.time() - t0, 2)})
             s.close()
     return {"case": f"planar Poiseuille, {ne}x{ne} quads, N={order}, D2Q9, u_max={umax:.6f}", "results": out}

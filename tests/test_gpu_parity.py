@@ -246,3 +246,19 @@ def test_poiseuille_walls_body_force(P, tau):
     slip_o = np.abs(u[wall, 0]).max() / umax
     slip_g = np.abs(ug.reshape(-1, 2)[np.abs(yl) < 1e-12, 0]).max() / umax
     assert slip_o > 0 and abs(slip_g - slip_o) <= 1e-9 * max(slip_o, 1e-3)
+
+
+def test_stress_matches_oracle(P):
+    """selbm_stress on a state set from the oracle (planar Poiseuille with walls and body force,
+    100 steps from the parabola): the non-equilibrium second moment within 1e-9 of the oracle."""
+    mesh = W.box_mesh((4, 4), (0, 0), (1, 1), (True, False), walls={2: 1, 3: 1}, wall_velocity=[[0, 0]])
+    probe = OracleSELBM(mesh, "D2Q9", 8, nu=1.0, cfl=0.5)
+    nu = 0.2 * probe.dt / 3.0
+    G = 8 * nu * (0.1 / 3.0)
+    init = W.poiseuille_init(G, nu)
+    o, s = pair(P, mesh, "D2Q9", 8, nu, g=(G, 0.0, 0.0), init=init)
+    f = o.run(o.initial_state_from(init), 100)
+    s.set_state(np.ascontiguousarray(o.to_local(f)))
+    pi_o = o.stress(f)[o.glo]
+    pi_g = s.stress()
+    assert rel(pi_g, pi_o) <= 1e-9

@@ -1,0 +1,46 @@
+"""Pins of the oracle's non-equilibrium second moment Pi (Sec. 3.3): zero at equilibrium (with
+a force), the Navier-Stokes shear stress rho nu u' of planar Poiseuille flow, and the normal
+stress -2 mu lambda (u')^2 that the paper quotes for it at the walls."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.lattice import CS2
+from oracle.selbm import OracleSELBM
+
+
+def poiseuille(tau, steps=400):
+    mesh = W.box_mesh((4, 4), (0, 0), (1, 1), (True, False), walls={2: 1, 3: 1}, wall_velocity=[[0, 0]])
+    probe = OracleSELBM(mesh, "D2Q9", 8, nu=1.0, cfl=0.5)
+    nu = tau * probe.dt * CS2
+    G = 8 * nu * (0.1 / 3)
+    o = OracleSELBM(mesh, "D2Q9", 8, nu=nu, cfl=0.5, body_accel=[G, 0.0])
+    f = o.run(o.initial_state_from(W.poiseuille_init(G, nu)), steps)
+    return o, f, nu, G
+
+
+def test_stress_zero_at_equilibrium():
+    mesh = W.box_mesh((2, 2), (0, 0), (1, 1), (True, True))
+    o = OracleSELBM(mesh, "D2Q9", 4, nu=0.01, body_accel=[2e-4, -1e-4])
+    rng = np.random.default_rng(6)
+    f = o.initial_state(1 + 0.01 * rng.standard_normal(o.G), 0.03 * rng.standard_normal((o.G, 2)))
+    assert np.abs(o.stress(f)).max() < 1e-15
+
+
+@pytest.mark.parametrize("tau", [0.1, 0.4])
+def test_poiseuille_shear_and_normal_stress(tau):
+    o, f, nu, G = poiseuille(tau)
+    rho, _ = o.moments(f)
+    y = o.Xg[:, 1]
+    dudy = G / (2 * nu) * (1 - 2 * y)
+    Pi = o.stress(f)
+    inner = (y > 0.05) & (y < 0.95)
+    sxy = rho * nu * dudy
+    assert np.abs(-Pi[inner, 0, 1] - sxy[inner]).max() < 2e-3 * np.abs(sxy).max()
+    lam = tau * o.dt
+    wall = np.abs(y) < 1e-12
+    txx = -Pi[wall, 0, 0]
+    expect = -2 * rho[wall] * nu * lam * dudy[wall] ** 2
+    assert np.abs(txx / expect - 1).max() < 0.1
