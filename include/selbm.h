@@ -346,8 +346,11 @@ int selbm_timers_read(selbm_t *h, double ms[SELBM_TIMER_KINDS], int64_t n[SELBM_
  * (e.g. on two streams at once) race and must be serialised by the caller.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Errors: SELBM_ERR_ARG (NULL pointer, bad sizes
- * or lattice), SELBM_ERR_CUDA (address lookup or launch failed).
+ * before any stream capture.  The address is kept for the life of the
+ * process: it does not survive a cudaDeviceReset of that device, so a process
+ * that resets a device must not call this entry point on it afterwards.
+ * Errors: SELBM_ERR_ARG (NULL pointer, bad sizes or lattice), SELBM_ERR_CUDA
+ * (address lookup or launch failed).
  */
 #define SELBM_NOALLOC_MAX_ELEMS 65536
 int selbm_integrals_noalloc(int32_t lattice, int32_t nelem, int32_t np, const double *f, const double *w,

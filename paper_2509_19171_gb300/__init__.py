@@ -20,6 +20,7 @@ D2Q9, D3Q19, D3Q27 = 0, 1, 2
 LATTICES = {"D2Q9": D2Q9, "D3Q19": D3Q19, "D3Q27": D3Q27}
 FP64, FP32DEV = 0, 1
 TIMER_KINDS = 5
+NOALLOC_MAX_ELEMS = 65536          # SELBM_NOALLOC_MAX_ELEMS of include/selbm.h
 TIMER_NAMES = ["stage1", "stage23", "assembly", "learned", "prologue"]
 ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_MESH", -3: "ERR_CUDA", -4: "ERR_NONFINITE", -5: "ERR_TIMEOUT", -6: "ERR_STATE"}
 

@@ -124,6 +124,9 @@ struct selbm {
     return SELBM_ERR_CUDA;
   }
   size_t nloc() const { return (size_t)S.E * S.Np; }
+  // population stride of the state arrays: G rounded up to a multiple of 8, so that every
+  // population row (and every element's interior block at N = 7) starts 16-byte aligned
+  int Gs() const { return (S.G + 7) & ~7; }
 };
 
 namespace {
@@ -132,16 +135,16 @@ template <typename Real>
 cudaError_t upload_real(selbm *h) {
   const Setup &S = h->S;
   cudaError_t e;
-  const size_t G = S.G, Q = h->Q;
+  const size_t G = S.G, GS = h->Gs(), Q = h->Q;
   auto alloc = [&](void **p, size_t bytes) {
     cudaError_t r = cudaMalloc(p, std::max<size_t>(bytes, 16));
     if (r == cudaSuccess) { h->allocs.push_back(*p); cudaMemsetAsync(*p, 0, std::max<size_t>(bytes, 16), h->stream); }
     return r;
   };
-  if ((e = alloc(&h->FA, Q * G * sizeof(Real)))) return e;
-  if ((e = alloc(&h->F0, Q * G * sizeof(Real)))) return e;
-  if ((e = alloc(&h->F2, Q * G * sizeof(Real)))) return e;
-  if ((e = alloc(&h->BUF, Q * G * sizeof(Real)))) return e;
+  if ((e = alloc(&h->FA, Q * GS * sizeof(Real)))) return e;
+  if ((e = alloc(&h->F0, Q * GS * sizeof(Real)))) return e;
+  if ((e = alloc(&h->F2, Q * GS * sizeof(Real)))) return e;
+  if ((e = alloc(&h->BUF, Q * GS * sizeof(Real)))) return e;
   if ((e = alloc(&h->T, Q * (size_t)S.E * S.Nb * sizeof(Real)))) return e;
   if ((e = alloc(&h->RHO, G * sizeof(Real)))) return e;
   Real *p;
@@ -224,7 +227,7 @@ template <typename Real>
 KParams<Real> base_params(selbm *h) {
   const Setup &S = h->S;
   KParams<Real> p{};
-  p.E = S.E; p.Np = S.Np; p.Nb = S.Nb; p.N = S.N; p.n = S.n1; p.G = S.G; p.Gb = S.Gb;
+  p.E = S.E; p.Np = S.Np; p.Nb = S.Nb; p.N = S.N; p.n = S.n1; p.G = S.G; p.Gs = h->Gs(); p.Gb = S.Gb;
   p.dt = (Real)h->dt; p.half_dt = (Real)(0.5 * h->dt); p.omega = (Real)h->omega; p.rho0 = (Real)h->P.rho0;
   for (int k = 0; k < 3; ++k) p.g[k] = (Real)(k < S.dim ? h->P.body_accel[k] : 0.0);
   p.has_force = h->has_force;
@@ -250,7 +253,7 @@ template <typename Real>
 cudaError_t enqueue_learned_filter(selbm *h, const Real *f, Real *out, bool with_drift) {
   const Setup &S = h->S;
   ControlArgs<Real> c{};
-  c.E = S.E; c.Np = S.Np; c.n = S.n1; c.N = S.N; c.G = S.G; c.Nb = S.Nb;
+  c.E = S.E; c.Np = S.Np; c.n = S.n1; c.N = S.N; c.G = S.G; c.Gs = h->Gs(); c.Nb = S.Nb;
   c.l2g = h->d_l2g; c.bslot = h->d_bslot; c.f = f; c.rho0 = h->P.rho0; c.affine = S.affine ? 1 : 0;
   c.el_J = (const Real *)h->d_el_J; c.wJ = (const Real *)h->d_wJ; c.gllw = (const Real *)h->d_gllw;
   c.Vm = (const Real *)h->d_Vm; c.Vinv = (const Real *)h->d_Vinv; c.W = h->d_W;
@@ -377,7 +380,7 @@ cudaError_t enqueue_step_printed(selbm *h, bool apply_filter) {
   KParams<Real> p = base_params<Real>(h);
   Real *FA = (Real *)h->FA, *F0 = (Real *)h->F0, *F1 = (Real *)h->F2;
   Real *F2 = (Real *)h->S1, *F3 = (Real *)h->S2, *GS = (Real *)h->SG, *BS = (Real *)h->SB;
-  const size_t nv = (size_t)h->Q * h->S.G;
+  const size_t nv = (size_t)h->Q * h->Gs();
   const double third[4] = {2.0 / 3.0, 0, 0, 0};
   cudaError_t e;
   // stage 1 (collision and pending filter included): f1 = f0 + dt/3 L f0
@@ -648,9 +651,9 @@ int selbm_init(selbm_t *h, const double *rho, const double *u, int on_device) {
   // the acceleration field enters the initial state with its time factor at t = 0
   const double amp0 = !h->field_on || !(0.0 < h->f_tend) ? 0.0 : (h->f_period > 0.0 ? 0.0 : 1.0);
   cudaError_t e = h->prec == SELBM_FP64
-                      ? launch_init<double>(h->lat, drho, du, h->d_first, h->S.G, h->P.rho0, 0.5 * h->dt, g, h->has_force,
+                      ? launch_init<double>(h->lat, drho, du, h->d_first, h->S.G, h->Gs(), h->P.rho0, 0.5 * h->dt, g, h->has_force,
                                             h->field_on ? (const double *)h->d_fS : nullptr, amp0, (double *)h->FA, h->stream)
-                      : launch_init<float>(h->lat, drho, du, h->d_first, h->S.G, h->P.rho0, 0.5 * h->dt, g, h->has_force,
+                      : launch_init<float>(h->lat, drho, du, h->d_first, h->S.G, h->Gs(), h->P.rho0, 0.5 * h->dt, g, h->has_force,
                                            h->field_on ? (const float *)h->d_fS : nullptr, amp0, (float *)h->FA, h->stream);
   if (e == cudaSuccess && h->d_ft) {
     h->ft_host = 0.0;
@@ -674,8 +677,8 @@ int selbm_set_state(selbm_t *h, const double *f, int on_device) {
     df = h->d_io;
   }
   cudaError_t e = h->prec == SELBM_FP64
-                      ? launch_set_state<double>(h->lat, df, h->d_first, h->S.G, nl, h->P.rho0, (double *)h->FA, h->stream)
-                      : launch_set_state<float>(h->lat, df, h->d_first, h->S.G, nl, h->P.rho0, (float *)h->FA, h->stream);
+                      ? launch_set_state<double>(h->lat, df, h->d_first, h->S.G, h->Gs(), nl, h->P.rho0, (double *)h->FA, h->stream)
+                      : launch_set_state<float>(h->lat, df, h->d_first, h->S.G, h->Gs(), nl, h->P.rho0, (float *)h->FA, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "set_state");
   h->initialized = true; h->filter_pending = false;
@@ -700,8 +703,8 @@ int selbm_get_state(selbm_t *h, double *f, int on_device) {
     df = h->d_io;
   }
   cudaError_t e = h->prec == SELBM_FP64
-                      ? launch_get_state<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, df, h->stream)
-                      : launch_get_state<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, df, h->stream);
+                      ? launch_get_state<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->Gs(), nl, h->P.rho0, df, h->stream)
+                      : launch_get_state<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->Gs(), nl, h->P.rho0, df, h->stream);
   if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(f, df, bytes, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "get_state");
@@ -771,8 +774,8 @@ int selbm_moments(selbm_t *h, double *rho, double *u, int on_device) {
     dr = h->d_io; du = h->d_io + nl;
   }
   cudaError_t e = h->prec == SELBM_FP64
-                      ? launch_moments<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, dr, du, h->stream)
-                      : launch_moments<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, dr, du, h->stream);
+                      ? launch_moments<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->Gs(), nl, h->P.rho0, dr, du, h->stream)
+                      : launch_moments<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->Gs(), nl, h->P.rho0, dr, du, h->stream);
   if (e == cudaSuccess && !on_device) {
     e = cudaMemcpyAsync(rho, dr, nl * 8, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(u, du, nl * d * 8, cudaMemcpyDeviceToHost, h->stream);
@@ -801,10 +804,10 @@ int selbm_stress(selbm_t *h, double *pi, int on_device) {
   const double factor = h->tau / (h->tau + 0.5);
   const double *g = h->P.body_accel;
   cudaError_t e = h->prec == SELBM_FP64
-                      ? launch_stress<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, 0.5 * h->dt,
+                      ? launch_stress<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->S.G, h->Gs(), nl, h->P.rho0, 0.5 * h->dt,
                                               factor, g, h->has_force, h->field_on ? (const double *)h->d_fS : nullptr,
                                               amp, dp, h->stream)
-                      : launch_stress<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, 0.5 * h->dt,
+                      : launch_stress<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->S.G, h->Gs(), nl, h->P.rho0, 0.5 * h->dt,
                                              factor, g, h->has_force, h->field_on ? (const float *)h->d_fS : nullptr,
                                              amp, dp, h->stream);
   if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(pi, dp, n * 8, cudaMemcpyDeviceToHost, h->stream);
@@ -819,7 +822,7 @@ int selbm_set_filter(selbm_t *h, const selbm_filter *f) {
     // the last step's filter (old settings) must be applied before switching
     int rc = finalize(h);
     if (rc) return rc;
-    size_t bytes = (size_t)h->Q * h->S.G * h->rsz;
+    size_t bytes = (size_t)h->Q * h->Gs() * h->rsz;
     cudaError_t e = cudaMemcpyAsync(h->FA, h->BUF, bytes, cudaMemcpyDeviceToDevice, h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "set_filter");
     h->filter_pending = false;
@@ -841,7 +844,7 @@ int selbm_set_time_scheme(selbm_t *h, int scheme) {
   if (scheme != 0) {
     // allocate whichever stage buffers are still missing (a failed call leaves the rest for
     // the next one)
-    const size_t bytes = (size_t)h->Q * h->S.G * h->rsz;
+    const size_t bytes = (size_t)h->Q * h->Gs() * h->rsz;
     void **bufs[4] = {&h->S1, &h->S2, &h->SG, &h->SB};
     for (void **b : bufs) {
       if (*b) continue;
@@ -905,8 +908,8 @@ int selbm_diagnostics(selbm_t *h, double out[8]) {
   int rc = finalize(h);
   if (rc) return rc;
   cudaError_t e = h->prec == SELBM_FP64
-                      ? launch_diag<double>(h->lat, (const double *)h->BUF, h->d_mass, h->S.G, h->P.rho0, h->d_partial, h->d_diag, h->stream)
-                      : launch_diag<float>(h->lat, (const float *)h->BUF, h->d_mass, h->S.G, h->P.rho0, h->d_partial, h->d_diag, h->stream);
+                      ? launch_diag<double>(h->lat, (const double *)h->BUF, h->d_mass, h->S.G, h->Gs(), h->P.rho0, h->d_partial, h->d_diag, h->stream)
+                      : launch_diag<float>(h->lat, (const float *)h->BUF, h->d_mass, h->S.G, h->Gs(), h->P.rho0, h->d_partial, h->d_diag, h->stream);
   // dissipation: velocity at local nodes, then per-element gradient integrals
   const size_t nl = h->nloc(), dim = h->S.dim;
   double *d_eps = nullptr;
@@ -916,8 +919,8 @@ int selbm_diagnostics(selbm_t *h, double out[8]) {
     d_eps = h->d_diag + 6;
     const double mu = h->P.rho0 * h->P.nu;
     e = h->prec == SELBM_FP64
-            ? launch_moments<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, rho_l, u_l, h->stream)
-            : launch_moments<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, rho_l, u_l, h->stream);
+            ? launch_moments<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->Gs(), nl, h->P.rho0, rho_l, u_l, h->stream)
+            : launch_moments<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->Gs(), nl, h->P.rho0, rho_l, u_l, h->stream);
     if (e == cudaSuccess)
       e = h->prec == SELBM_FP64
               ? launch_eps<double>(u_l, (int)dim, h->S.n1, h->S.Np, h->S.E, h->S.affine, (const double *)h->d_el_drdx,
@@ -955,8 +958,8 @@ int selbm_wall_stress(selbm_t *h, const double dir[3], double *tau) {
   double *rho_l = h->d_io, *u_l = h->d_io + nl, *part = h->d_io + nl * (1 + dim);
   const double mu = h->P.rho0 * h->P.nu;
   cudaError_t e = h->prec == SELBM_FP64
-                      ? launch_moments<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, rho_l, u_l, h->stream)
-                      : launch_moments<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, rho_l, u_l, h->stream);
+                      ? launch_moments<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->Gs(), nl, h->P.rho0, rho_l, u_l, h->stream)
+                      : launch_moments<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->Gs(), nl, h->P.rho0, rho_l, u_l, h->stream);
   if (e == cudaSuccess)
     e = h->prec == SELBM_FP64
             ? launch_wall_stress<double>(u_l, dim, h->S.n1, h->S.Np, h->S.E, h->S.affine, (const double *)h->d_el_drdx,
@@ -1002,8 +1005,8 @@ int selbm_radial_profile(selbm_t *h, const double origin[3], const double axis[3
   if ((rc = ensure_io(h, (nl * (1 + dim) + (size_t)blocks * 2 * nbins) * 8))) return rc;
   double *rho_l = h->d_io, *u_l = h->d_io + nl, *part = h->d_io + nl * (1 + dim);
   e = h->prec == SELBM_FP64
-          ? launch_moments<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, rho_l, u_l, h->stream)
-          : launch_moments<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->S.G, nl, h->P.rho0, rho_l, u_l, h->stream);
+          ? launch_moments<double>(h->lat, (const double *)h->BUF, h->d_l2g, h->Gs(), nl, h->P.rho0, rho_l, u_l, h->stream)
+          : launch_moments<float>(h->lat, (const float *)h->BUF, h->d_l2g, h->Gs(), nl, h->P.rho0, rho_l, u_l, h->stream);
   if (e == cudaSuccess)
     e = launch_radial_profile(u_l, dim, h->d_first, h->d_xg, h->d_mass, h->S.G, o, a, radius, nbins, blocks, part,
                               h->stream);
@@ -1088,7 +1091,7 @@ int selbm_set_learned_filter(selbm_t *h, const float *params, const float *lo, c
     // apply the pending filter with the old settings first
     int rc = finalize(h);
     if (rc) return rc;
-    cudaError_t e = cudaMemcpyAsync(h->FA, h->BUF, (size_t)h->Q * h->S.G * h->rsz, cudaMemcpyDeviceToDevice, h->stream);
+    cudaError_t e = cudaMemcpyAsync(h->FA, h->BUF, (size_t)h->Q * h->Gs() * h->rsz, cudaMemcpyDeviceToDevice, h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "set_learned_filter");
     h->filter_pending = false;
   }
@@ -1124,7 +1127,7 @@ int selbm_clear_learned_filter(selbm_t *h) {
   if (h->learned && h->filter_pending) {
     int rc = finalize(h);
     if (rc) return rc;
-    cudaError_t e = cudaMemcpyAsync(h->FA, h->BUF, (size_t)h->Q * h->S.G * h->rsz, cudaMemcpyDeviceToDevice, h->stream);
+    cudaError_t e = cudaMemcpyAsync(h->FA, h->BUF, (size_t)h->Q * h->Gs() * h->rsz, cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "clear_learned_filter");
     h->filter_pending = false;
@@ -1171,7 +1174,7 @@ int selbm_features(selbm_t *h, float *feat) {
     using Real = decltype(tag);
     const Setup &S = h->S;
     ControlArgs<Real> c{};
-    c.E = S.E; c.Np = S.Np; c.n = S.n1; c.N = S.N; c.G = S.G; c.Nb = S.Nb;
+    c.E = S.E; c.Np = S.Np; c.n = S.n1; c.N = S.N; c.G = S.G; c.Gs = h->Gs(); c.Nb = S.Nb;
     c.l2g = h->d_l2g; c.bslot = h->d_bslot; c.f = (const Real *)h->FA; c.rho0 = h->P.rho0; c.affine = S.affine ? 1 : 0;
     c.el_J = (const Real *)h->d_el_J; c.wJ = (const Real *)h->d_wJ; c.gllw = (const Real *)h->d_gllw;
     c.Vm = (const Real *)h->d_Vm; c.Vinv = (const Real *)h->d_Vinv; c.W = nullptr; c.sigma_out = nullptr; c.feat_out = feat;

@@ -148,6 +148,7 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   const Real Bdt = p.B * p.dt;
   const int32_t *l2g = p.l2g + (size_t)e * Np;
   const size_t G = p.G;
+  const size_t GS = p.Gs;                         // population stride of the state
 
   // ---- per-element constants
   __shared__ int s_r;
@@ -186,7 +187,7 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
       const size_t g = l2g[i];
       const int ti = TI::node(i);
 #pragma unroll
-      for (int a = 0; a < Q; ++a) sf[a * PS + ti] = fin[(size_t)a * G + g];
+      for (int a = 0; a < Q; ++a) sf[a * PS + ti] = fin[(size_t)a * GS + g];
       if (!AFFINE) {
         const Real *gm = p.drdx + ((size_t)e * Np + i) * DIM * DIM;
 #pragma unroll
@@ -288,7 +289,7 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
         const Real fa = f(a);
         const Real out = fa - p.omega * (fa - feq) + p.dt * Fss;
         sf[a * PS + ti] = out;
-        if (own) p.f0out[(size_t)a * G + gid] = out;
+        if (own) p.f0out[(size_t)a * GS + gid] = out;
       });
       if (own && p.has_force) p.rho[gid] = rho;
     }
@@ -498,16 +499,16 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
         if (p.stage != 1) {
 #pragma unroll
           for (int a = 0; a < Q; ++a) {
-            Real out = sf[a * PS + ti] + p.A * f0p[(size_t)a * G];
+            Real out = sf[a * PS + ti] + p.A * f0p[(size_t)a * GS];
             if (p.has_force) out += force(a);
-            fo[(size_t)a * G] = out;
+            fo[(size_t)a * GS] = out;
           }
         } else {
 #pragma unroll
           for (int a = 0; a < Q; ++a) {
             Real out = sf[a * PS + ti];
             if (p.has_force) out += force(a);
-            fo[(size_t)a * G] = out;
+            fo[(size_t)a * GS] = out;
           }
         }
       } else {

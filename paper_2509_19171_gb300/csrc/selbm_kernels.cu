@@ -131,7 +131,7 @@ __device__ void collide_node(Real *sf, int i, const KParams<Real> &p, Real *srho
     const Real v = sf[a * Np + i];
     const Real out = v - p.omega * (v - feq) + p.dt * Fss;
     sf[a * Np + i] = out;
-    if (own) p.f0out[a * (size_t)p.G + gid] = out;
+    if (own) p.f0out[a * (size_t)p.Gs + gid] = out;
   }
   srho[i] = rho;
   if (own && p.has_force) p.rho[gid] = rho;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(512) stage_kernel(const KParams<Real> p) {
   const int32_t *l2g = p.l2g + (size_t)e * Np;
   for (int idx = tid; idx < Q * Np; idx += nt) {
     const int a = idx / Np, i = idx - a * Np;
-    sf[idx] = p.fin[(size_t)a * p.G + l2g[i]];
+    sf[idx] = p.fin[(size_t)a * p.Gs + l2g[i]];
   }
   __syncthreads();
   if (p.stage == 1) {
@@ -221,8 +221,8 @@ __global__ void __launch_bounds__(512) stage_kernel(const KParams<Real> p) {
         Fs = wt<Real>(LAT, a) * eg * rho_i * ics2;
       }
       const Real fprev = sf[idx];
-      const Real f0v = p.stage == 1 ? fprev : p.f0[(size_t)a * p.G + gid];
-      p.fout[(size_t)a * p.G + gid] = p.A * f0v + p.B * (fprev + p.dt * (Fs - adv));
+      const Real f0v = p.stage == 1 ? fprev : p.f0[(size_t)a * p.Gs + gid];
+      p.fout[(size_t)a * p.Gs + gid] = p.A * f0v + p.B * (fprev + p.dt * (Fs - adv));
     } else {
       Real wJi;
       if (AFFINE) {
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) dss_kernel(con
   const Real *__restrict__ fin = p.fin;
   const Real *__restrict__ f0 = p.f0;
   Real *__restrict__ fout = p.fout;
-  const size_t G = p.G;
+  const size_t G = p.Gs;                 // population stride
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < p.Gb; u += gridDim.x * blockDim.x) {
     const int c0 = p.bnode_off[u], c1 = p.bnode_off[u + 1];
     const size_t gid = p.bnode_g[u];
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(512) finalize_kernel(const KParams<Real> p) {
   const int32_t *l2g = p.l2g + (size_t)e * Np;
   for (int idx = tid; idx < Q * Np; idx += nt) {
     const int a = idx / Np, i = idx - a * Np;
-    sf[idx] = p.fin[(size_t)a * p.G + l2g[i]];
+    sf[idx] = p.fin[(size_t)a * p.Gs + l2g[i]];
   }
   __syncthreads();
   if (p.apply_filter) {
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(512) finalize_kernel(const KParams<Real> p) {
   }
   for (int idx = tid; idx < Q * Np; idx += nt) {
     const int a = idx / Np, i = idx - a * Np;
-    if (p.owner[(size_t)e * Np + i]) p.fout[(size_t)a * p.G + l2g[i]] = sf[idx];
+    if (p.owner[(size_t)e * Np + i]) p.fout[(size_t)a * p.Gs + l2g[i]] = sf[idx];
   }
 }
 
@@ -424,7 +424,7 @@ cudaError_t launch_finalize(int lat, const KParams<Real> &p, cudaStream_t s) {
 
 // f_bar = f^eq(rho, u) - dt/2 F** stored as g = f_bar - t rho0 (Sec. 2.1, f at equilibrium)
 template <typename Real, int LAT>
-__global__ void init_kernel(const double *rho, const double *u, const int32_t *first, int G, double rho0,
+__global__ void init_kernel(const double *rho, const double *u, const int32_t *first, int G, int Gs, double rho0,
                             double half_dt, double gx, double gy, double gz, int has_force, const Real *fS,
                             double amp, Real *out) {
   constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
@@ -447,34 +447,34 @@ __global__ void init_kernel(const double *rho, const double *u, const int32_t *f
       const double t = c_td[LAT][a];
       const double feq = t * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
       const double Fss = t * (9.0 * eu * eF - 3.0 * uF);
-      out[(size_t)a * G + g] = (Real)(feq - half_dt * Fss - t * rho0);
+      out[(size_t)a * Gs + g] = (Real)(feq - half_dt * Fss - t * rho0);
     }
   }
 }
 
 template <typename Real, int LAT>
-__global__ void set_state_kernel(const double *f, const int32_t *first, int G, size_t nloc, double rho0, Real *out) {
+__global__ void set_state_kernel(const double *f, const int32_t *first, int G, int Gs, size_t nloc, double rho0, Real *out) {
   constexpr int Q = Lat<LAT>::Q;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
-    for (int a = 0; a < Q; ++a) out[(size_t)a * G + g] = (Real)(f[(size_t)a * nloc + first[g]] - c_td[LAT][a] * rho0);
+    for (int a = 0; a < Q; ++a) out[(size_t)a * Gs + g] = (Real)(f[(size_t)a * nloc + first[g]] - c_td[LAT][a] * rho0);
 }
 
 template <typename Real, int LAT>
-__global__ void get_state_kernel(const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double *f) {
+__global__ void get_state_kernel(const Real *buf, const int32_t *l2g, int Gs, size_t nloc, double rho0, double *f) {
   constexpr int Q = Lat<LAT>::Q;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nloc; q += (size_t)gridDim.x * blockDim.x)
-    for (int a = 0; a < Q; ++a) f[(size_t)a * nloc + q] = (double)buf[(size_t)a * G + l2g[q]] + c_td[LAT][a] * rho0;
+    for (int a = 0; a < Q; ++a) f[(size_t)a * nloc + q] = (double)buf[(size_t)a * Gs + l2g[q]] + c_td[LAT][a] * rho0;
 }
 
 // rho = sum f_bar, rho u = sum e f_bar at every local node (FP64 sums)
 template <typename Real, int LAT>
-__global__ void moments_kernel(const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double *rho, double *u) {
+__global__ void moments_kernel(const Real *buf, const int32_t *l2g, int Gs, size_t nloc, double rho0, double *rho, double *u) {
   constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nloc; q += (size_t)gridDim.x * blockDim.x) {
     const size_t g = l2g[q];
     double d = 0, j[3] = {0, 0, 0};
     for (int a = 0; a < Q; ++a) {
-      const double v = (double)buf[(size_t)a * G + g];
+      const double v = (double)buf[(size_t)a * Gs + g];
       d += v;
       for (int k = 0; k < DIM; ++k) j[k] += c_e[LAT][a][k] * v;
     }
@@ -488,7 +488,7 @@ __global__ void moments_kernel(const Real *buf, const int32_t *l2g, int G, size_
 // + dt/2 F**_a), factor = tau / (tau + 1/2); the buffer holds deviations f - t rho0; acceleration
 // g + amp S_g (amp the field's time factor at the read-back time)
 template <typename Real, int LAT>
-__global__ void stress_kernel(const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double half_dt,
+__global__ void stress_kernel(const Real *buf, const int32_t *l2g, int G, int Gs, size_t nloc, double rho0, double half_dt,
                               double factor, double g0, double g1, double g2, int has_force, const Real *fS, double amp,
                               double *out) {
   constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
@@ -496,7 +496,7 @@ __global__ void stress_kernel(const Real *buf, const int32_t *l2g, int G, size_t
     const size_t g = l2g[q];
     double d = 0, j[3] = {0, 0, 0};
     for (int a = 0; a < Q; ++a) {
-      const double v = (double)buf[(size_t)a * G + g];
+      const double v = (double)buf[(size_t)a * Gs + g];
       d += v;
       for (int k = 0; k < DIM; ++k) j[k] += c_e[LAT][a][k] * v;
     }
@@ -515,8 +515,10 @@ __global__ void stress_kernel(const Real *buf, const int32_t *l2g, int G, size_t
       double eu = 0, eF = 0;
       for (int k = 0; k < DIM; ++k) { eu += c_e[LAT][a][k] * u[k]; eF += c_e[LAT][a][k] * F[k]; }
       const double t = c_td[LAT][a];
-      // f - f^eq with f = buf + t rho0 and f^eq = t rho (1 + 3 eu + 4.5 eu^2 - 1.5 uu), rho = rho0 + d
-      const double neq = (double)buf[(size_t)a * G + g] - t * (d + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu)) +
+      // f - f^eq with f = buf + t rho0 and f^eq = t rho (1 + 3 eu + 4.5 eu^2 - 1.5 uu), rho = rho0 + d;
+      // f_bar^eq = f^eq - dt/2 F** enters as + dt/2 F** without the 3 e.F term of F**: that
+      // term's second moment sum_a t_a e_ai e_aj e_ak F_k vanishes, so it cannot change Pi
+      const double neq = (double)buf[(size_t)a * Gs + g] - t * (d + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu)) +
                          half_dt * t * (9.0 * eu * eF - 3.0 * uF);
       for (int i = 0; i < DIM; ++i)
         for (int k = 0; k < DIM; ++k) pi[i][k] += (double)(c_e[LAT][a][i] * c_e[LAT][a][k]) * neq;
@@ -528,14 +530,14 @@ __global__ void stress_kernel(const Real *buf, const int32_t *l2g, int G, size_t
 
 // per-block partial sums: mass, momentum[3], KE, non-finite count (deterministic two-pass)
 template <typename Real, int LAT>
-__global__ void diag_partial_kernel(const Real *buf, const double *mass, int G, double rho0, double *partial) {
+__global__ void diag_partial_kernel(const Real *buf, const double *mass, int G, int Gs, double rho0, double *partial) {
   constexpr int Q = Lat<LAT>::Q, DIM = Lat<LAT>::D;
   __shared__ double red[6][256];
   double acc[6] = {0, 0, 0, 0, 0, 0};
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
     double d = 0, j[3] = {0, 0, 0};
     for (int a = 0; a < Q; ++a) {
-      const double v = (double)buf[(size_t)a * G + g];
+      const double v = (double)buf[(size_t)a * Gs + g];
       if (!isfinite(v)) acc[5] += 1.0;
       d += v;
       for (int k = 0; k < DIM; ++k) j[k] += c_e[LAT][a][k] * v;
@@ -660,10 +662,10 @@ static int grid_for(size_t n, int threads) { return (int)std::min<size_t>((n + t
   }
 
 template <typename Real>
-cudaError_t launch_init(int lat, const double *rho, const double *u, const int32_t *first, int G, double rho0,
+cudaError_t launch_init(int lat, const double *rho, const double *u, const int32_t *first, int G, int Gs, double rho0,
                         double half_dt, const double g[3], int has_force, const Real *fS, double amp, Real *out,
                         cudaStream_t s) {
-  SELBM_LAT_SWITCH(lat, (init_kernel<Real, L><<<grid_for(G, 256), 256, 0, s>>>(rho, u, first, G, rho0, half_dt, g[0], g[1], g[2], has_force, fS, amp, out)));
+  SELBM_LAT_SWITCH(lat, (init_kernel<Real, L><<<grid_for(G, 256), 256, 0, s>>>(rho, u, first, G, Gs, rho0, half_dt, g[0], g[1], g[2], has_force, fS, amp, out)));
   return cudaGetLastError();
 }
 
@@ -719,49 +721,49 @@ cudaError_t launch_force_amp(double *ft, Real *amp, double dt, double period, do
   return cudaGetLastError();
 }
 template <typename Real>
-cudaError_t launch_set_state(int lat, const double *f, const int32_t *first, int G, size_t nloc, double rho0, Real *out, cudaStream_t s) {
-  SELBM_LAT_SWITCH(lat, (set_state_kernel<Real, L><<<grid_for(G, 256), 256, 0, s>>>(f, first, G, nloc, rho0, out)));
+cudaError_t launch_set_state(int lat, const double *f, const int32_t *first, int G, int Gs, size_t nloc, double rho0, Real *out, cudaStream_t s) {
+  SELBM_LAT_SWITCH(lat, (set_state_kernel<Real, L><<<grid_for(G, 256), 256, 0, s>>>(f, first, G, Gs, nloc, rho0, out)));
   return cudaGetLastError();
 }
 template <typename Real>
-cudaError_t launch_get_state(int lat, const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double *f, cudaStream_t s) {
-  SELBM_LAT_SWITCH(lat, (get_state_kernel<Real, L><<<grid_for(nloc, 256), 256, 0, s>>>(buf, l2g, G, nloc, rho0, f)));
+cudaError_t launch_get_state(int lat, const Real *buf, const int32_t *l2g, int Gs, size_t nloc, double rho0, double *f, cudaStream_t s) {
+  SELBM_LAT_SWITCH(lat, (get_state_kernel<Real, L><<<grid_for(nloc, 256), 256, 0, s>>>(buf, l2g, Gs, nloc, rho0, f)));
   return cudaGetLastError();
 }
 template <typename Real>
-cudaError_t launch_moments(int lat, const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double *rho, double *u, cudaStream_t s) {
-  SELBM_LAT_SWITCH(lat, (moments_kernel<Real, L><<<grid_for(nloc, 256), 256, 0, s>>>(buf, l2g, G, nloc, rho0, rho, u)));
+cudaError_t launch_moments(int lat, const Real *buf, const int32_t *l2g, int Gs, size_t nloc, double rho0, double *rho, double *u, cudaStream_t s) {
+  SELBM_LAT_SWITCH(lat, (moments_kernel<Real, L><<<grid_for(nloc, 256), 256, 0, s>>>(buf, l2g, Gs, nloc, rho0, rho, u)));
   return cudaGetLastError();
 }
 template <typename Real>
-cudaError_t launch_stress(int lat, const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double half_dt,
+cudaError_t launch_stress(int lat, const Real *buf, const int32_t *l2g, int G, int Gs, size_t nloc, double rho0, double half_dt,
                           double factor, const double g[3], int has_force, const Real *fS, double amp, double *out,
                           cudaStream_t s) {
   SELBM_LAT_SWITCH(lat, (stress_kernel<Real, L><<<grid_for(nloc, 256), 256, 0, s>>>(
-                             buf, l2g, G, nloc, rho0, half_dt, factor, g[0], g[1], g[2], has_force, fS, amp, out)));
+                             buf, l2g, G, Gs, nloc, rho0, half_dt, factor, g[0], g[1], g[2], has_force, fS, amp, out)));
   return cudaGetLastError();
 }
 int diag_blocks() { return 152 * 4; }
 template <typename Real>
-cudaError_t launch_diag(int lat, const Real *buf, const double *mass, int G, double rho0, double *partial, double *out, cudaStream_t s) {
-  SELBM_LAT_SWITCH(lat, (diag_partial_kernel<Real, L><<<diag_blocks(), 256, 0, s>>>(buf, mass, G, rho0, partial)));
+cudaError_t launch_diag(int lat, const Real *buf, const double *mass, int G, int Gs, double rho0, double *partial, double *out, cudaStream_t s) {
+  SELBM_LAT_SWITCH(lat, (diag_partial_kernel<Real, L><<<diag_blocks(), 256, 0, s>>>(buf, mass, G, Gs, rho0, partial)));
   diag_final_kernel<<<1, 32, 0, s>>>(partial, diag_blocks(), out);
   return cudaGetLastError();
 }
 
 #define SELBM_INST_UTIL(Real)                                                                                              \
-  template cudaError_t launch_init<Real>(int, const double *, const double *, const int32_t *, int, double, double,      \
+  template cudaError_t launch_init<Real>(int, const double *, const double *, const int32_t *, int, int, double, double,      \
                                          const double[3], int, const Real *, double, Real *, cudaStream_t);              \
   template cudaError_t launch_force_field<Real>(const double *, const int32_t *, int, int, Real *, cudaStream_t);         \
   template cudaError_t launch_combine<Real>(size_t, const Real *, const Real *, const Real *, const Real *, int,         \
                                             const double[4], const Real *, double, Real *, Real *, cudaStream_t);        \
   template cudaError_t launch_force_amp<Real>(double *, Real *, double, double, double, cudaStream_t);                    \
-  template cudaError_t launch_stress<Real>(int, const Real *, const int32_t *, int, size_t, double, double, double,        \
+  template cudaError_t launch_stress<Real>(int, const Real *, const int32_t *, int, int, size_t, double, double, double,        \
                                            const double[3], int, const Real *, double, double *, cudaStream_t);          \
-  template cudaError_t launch_set_state<Real>(int, const double *, const int32_t *, int, size_t, double, Real *, cudaStream_t); \
+  template cudaError_t launch_set_state<Real>(int, const double *, const int32_t *, int, int, size_t, double, Real *, cudaStream_t); \
   template cudaError_t launch_get_state<Real>(int, const Real *, const int32_t *, int, size_t, double, double *, cudaStream_t); \
   template cudaError_t launch_moments<Real>(int, const Real *, const int32_t *, int, size_t, double, double *, double *, cudaStream_t); \
-  template cudaError_t launch_diag<Real>(int, const Real *, const double *, int, double, double *, double *, cudaStream_t);
+  template cudaError_t launch_diag<Real>(int, const Real *, const double *, int, int, double, double *, double *, cudaStream_t);
 SELBM_INST_UTIL(double)
 SELBM_INST_UTIL(float)
 

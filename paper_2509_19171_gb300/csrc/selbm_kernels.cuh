@@ -3,6 +3,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cstdlib>
 
 #include "../../include/selbm.h"
 
@@ -20,6 +21,7 @@ struct WallPt {
 template <typename Real>
 struct KParams {
   int E, Np, Nb, N, n, G, Gb;
+  int Gs;                    // population stride of the state arrays (G rounded up to a multiple of 8)
   int stage;                 // 1, 2, 3
   Real A, B;                 // f^s = A f^0 + B (f^{s-1} + dt L(f^{s-1}))
   Real dt, omega, rho0, half_dt;
@@ -75,7 +77,7 @@ template <typename Real>
 cudaError_t launch_finalize(int lat, const KParams<Real> &p, cudaStream_t s);
 
 template <typename Real>
-cudaError_t launch_init(int lat, const double *rho, const double *u, const int32_t *first, int G, double rho0,
+cudaError_t launch_init(int lat, const double *rho, const double *u, const int32_t *first, int G, int Gs, double rho0,
                         double half_dt, const double g[3], int has_force, const Real *fS, double amp, Real *out,
                         cudaStream_t s);
 // g = sum_{i < m} c_i f_i and b = base - cb g over n values (m <= 4): the argument of a stage
@@ -89,21 +91,21 @@ template <typename Real>
 cudaError_t launch_force_field(const double *S, const int32_t *first, int G, int dim, Real *fS, cudaStream_t s);
 // non-equilibrium second moment at every local node, out [nloc][dim][dim]
 template <typename Real>
-cudaError_t launch_stress(int lat, const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double half_dt,
+cudaError_t launch_stress(int lat, const Real *buf, const int32_t *l2g, int G, int Gs, size_t nloc, double rho0, double half_dt,
                           double factor, const double g[3], int has_force, const Real *fS, double amp, double *out,
                           cudaStream_t s);
 // time factor of the field for the step starting at ft[0]; advances ft[0] by dt
 template <typename Real>
 cudaError_t launch_force_amp(double *ft, Real *amp, double dt, double period, double t_end, cudaStream_t s);
 template <typename Real>
-cudaError_t launch_set_state(int lat, const double *f, const int32_t *first, int G, size_t nloc, double rho0, Real *out, cudaStream_t s);
+cudaError_t launch_set_state(int lat, const double *f, const int32_t *first, int G, int Gs, size_t nloc, double rho0, Real *out, cudaStream_t s);
 template <typename Real>
-cudaError_t launch_get_state(int lat, const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double *f, cudaStream_t s);
+cudaError_t launch_get_state(int lat, const Real *buf, const int32_t *l2g, int Gs, size_t nloc, double rho0, double *f, cudaStream_t s);
 template <typename Real>
-cudaError_t launch_moments(int lat, const Real *buf, const int32_t *l2g, int G, size_t nloc, double rho0, double *rho, double *u, cudaStream_t s);
+cudaError_t launch_moments(int lat, const Real *buf, const int32_t *l2g, int Gs, size_t nloc, double rho0, double *rho, double *u, cudaStream_t s);
 int diag_blocks();
 template <typename Real>
-cudaError_t launch_diag(int lat, const Real *buf, const double *mass, int G, double rho0, double *partial, double *out, cudaStream_t s);
+cudaError_t launch_diag(int lat, const Real *buf, const double *mass, int G, int Gs, double rho0, double *partial, double *out, cudaStream_t s);
 
 // host copies of the matrices of the register-blocked stage kernel
 struct FastHost {

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) control_kernel(const ControlArgs<Real> c)
     Real drho = 0, j[3] = {0, 0, 0};
     static_for<0, Q>([&](auto ac) {
       constexpr int a = decltype(ac)::value;
-      const Real v = c.f[(size_t)a * c.G + g];
+      const Real v = c.f[(size_t)a * c.Gs + g];
       sf[a * Np + i] = v;
       drho += v;
 #pragma unroll
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) control_kernel(const ControlArgs<Real> c)
   for (int idx = tid; idx < Q * Np; idx += T) {
     const int a = idx / Np, i = idx - a * Np;
     const int b = c.bslot[i];
-    if (b < 0) c.fout[(size_t)a * c.G + l2g[i]] = sf[idx];
+    if (b < 0) c.fout[(size_t)a * c.Gs + l2g[i]] = sf[idx];
     else c.T[a * EN + (size_t)e * c.Nb + b] = weight(i) * sf[idx];
   }
 }

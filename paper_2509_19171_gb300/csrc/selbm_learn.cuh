@@ -11,6 +11,7 @@ namespace slb {
 template <typename Real>
 struct ControlArgs {
   int E, Np, n, N, G, Nb;
+  int Gs;                      // population stride of the state arrays
   const int32_t *l2g;          // [E][Np]
   const int32_t *bslot;        // [Np] boundary slot of each local node, -1 inside
   const Real *f;               // state on unique nodes [Q][G] (deviation form)

@@ -241,7 +241,7 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
   __shared__ int s_r, in_range, s_mode[n];
   const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int32_t *l2g = p.l2g + (size_t)e * Np;
-  const size_t G = p.G;
+  const size_t G = p.Gs;                            // population stride of the state
   auto weight = [&](int i) -> Real {
     if (AFFINE) {
       const int i0 = i % n, i1 = (i / n) % n, i2 = i / (n * n);
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(256) dss_collide_kernel(const KParams<Real> p)
     node_accel(p, gid, gacc);
     const Real rho = bgk_collide<Real, LAT>(s, p.rho0, p.omega, p.dt, p.half_dt, gacc, p.has_force != 0);
 #pragma unroll
-    for (int a = 0; a < Q; ++a) p.f0out[(size_t)a * p.G + gid] = s[a];
+    for (int a = 0; a < Q; ++a) p.f0out[(size_t)a * p.Gs + gid] = s[a];
     if (p.has_force) p.rho[gid] = rho;
   }
 }
@@ -513,11 +513,11 @@ __global__ void __launch_bounds__(256) collide_nodes_kernel(const KParams<Real> 
   for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < (size_t)p.G; g += (size_t)gridDim.x * blockDim.x) {
     Real s[Q], gacc[3];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) s[a] = p.fin[(size_t)a * p.G + g];
+    for (int a = 0; a < Q; ++a) s[a] = p.fin[(size_t)a * p.Gs + g];
     node_accel(p, g, gacc);
     const Real rho = bgk_collide<Real, LAT>(s, p.rho0, p.omega, p.dt, p.half_dt, gacc, p.has_force != 0);
 #pragma unroll
-    for (int a = 0; a < Q; ++a) p.f0out[(size_t)a * p.G + g] = s[a];
+    for (int a = 0; a < Q; ++a) p.f0out[(size_t)a * p.Gs + g] = s[a];
     if (p.has_force) p.rho[g] = rho;
   }
 }
@@ -549,11 +549,11 @@ FastMats<Real, n> make_fast_mats(const SplitHost &h) {
     }                                                                                            \
   } while (0)
 
-template <typename Real, int LAT, int n, bool AFFINE>
+template <typename Real, int LAT, int n, bool AFFINE, int PBW = 0>
 cudaError_t launch_split_t(const KParams<Real> &p, const SplitHost &h, cudaStream_t s) {
-  using S = SplitShape<LAT, n>;
-  const size_t smem = split_smem_bytes<Real, LAT, n, AFFINE>(p.wall_max);
-  auto k = stage_split_kernel<Real, LAT, n, AFFINE>;
+  using S = SplitShape<LAT, n, PBW>;
+  const size_t smem = split_smem_bytes<Real, LAT, n, AFFINE, PBW>(p.wall_max);
+  auto k = stage_split_kernel<Real, LAT, n, AFFINE, PBW>;
   SLB_SET_SMEM_ONCE(k, smem);
   k<<<p.E * S::NG, S::THREADS, smem, s>>>(p, make_fast_mats<Real, n>(h));
   return cudaGetLastError();

@@ -18,21 +18,22 @@ __device__ __forceinline__ void cp_async(Real *dst, const Real *src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <int LAT, int n>
+template <int LAT, int n, int PBW = 0>
 struct SplitShape {
   static constexpr int Q = LT<LAT>::v.Q;
   static constexpr int Np = n * n * n, NL = n * n;
   static constexpr int LPR = 256 / NL < 1 ? 1 : 256 / NL;         // populations per round of tasks
-  static constexpr int THREADS = LPR * NL;                        // one (population, r-line) task per round
+  // PBW > 0 (swizzled FP32 tile, one warp per population): PBW populations per work item
+  static constexpr int THREADS = PBW > 0 ? 32 * PBW : LPR * NL;   // one (population, r-line) task per round
   static constexpr int ROUNDS = 2;
-  static constexpr int PB = ROUNDS * LPR;                         // populations per work item
+  static constexpr int PB = PBW > 0 ? PBW : ROUNDS * LPR;         // populations per work item
   static constexpr int NG = (Q + PB - 1) / PB;                    // work items per element
   static constexpr int NPT = (Np + THREADS - 1) / THREADS;        // nodes per thread when gathering
 };
 
-template <typename Real, int LAT, int n, bool AFFINE>
+template <typename Real, int LAT, int n, bool AFFINE, int PBW = 0>
 constexpr size_t split_smem_bytes(int wall_max) {
-  using S = SplitShape<LAT, n>;
+  using S = SplitShape<LAT, n, PBW>;
   using TI = Tile<Real, n, 3>;
   size_t reals = 2 * (size_t)S::PB * TI::PS + n * n + S::PB * 3 + 2 * S::PB + n;
   if (!AFFINE) reals += (size_t)S::Np * 10;
@@ -79,10 +80,10 @@ __device__ __forceinline__ void cp_async_s(unsigned dst, const Real *src) {
 // ---------------------------------------------------------------------------
 // one Runge-Kutta stage for PB populations of one element
 // ---------------------------------------------------------------------------
-template <typename Real, int LAT, int n, bool AFFINE>
-__global__ void __launch_bounds__(SplitShape<LAT, n>::THREADS, (sizeof(Real) == 4 ? (AFFINE ? 5 : 4) : 2))
+template <typename Real, int LAT, int n, bool AFFINE, int PBW = 0>
+__global__ void __launch_bounds__(SplitShape<LAT, n, PBW>::THREADS, (sizeof(Real) == 4 ? (PBW > 8 ? 4 : (AFFINE ? 5 : 4)) : 2))
 stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
-  using S = SplitShape<LAT, n>;
+  using S = SplitShape<LAT, n, PBW>;
   constexpr int Q = S::Q, DIM = 3, Np = S::Np, NL = S::NL, T = S::THREADS, PB = S::PB, NG = S::NG;
   constexpr int NPT = S::NPT, LPR = S::LPR, ROUNDS = S::ROUNDS;
   using TI = Tile<Real, n, DIM>;
@@ -107,7 +108,7 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   const int tid = threadIdx.x;
   const Real Bdt = p.B * p.dt;
   const int32_t *l2g = p.l2g + (size_t)e * Np;
-  const size_t G = p.G;
+  const size_t G = p.Gs;                            // population stride of the state
   const bool use_f0 = p.stage != 1;
 
   // ---- gather f^{s-1} of the group (and f^0 of element-interior nodes) with asynchronous
@@ -542,7 +543,8 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
           } else if (p.has_force) {
             const Real rg = p.rho[g];
             const Real A = *p.famp;                 // A(t) S_g of the per-node field
-            const Real sx[3] = {A * p.fS[g], A * p.fS[G + g], A * p.fS[2 * G + g]};
+            const size_t GN = p.G;                   // the field is per node: [3][G]
+            const Real sx[3] = {A * p.fS[g], A * p.fS[GN + g], A * p.fS[2 * GN + g]};
 #pragma unroll
             for (int pl = 0; pl < PB; ++pl)
               if (pl < na) {

@@ -100,3 +100,11 @@ def test_single_element_periodic(P):
     assert info["G"] == 25
     o = OracleSELBM(mesh, "D2Q9", 5, nu=0.01)
     assert o.G == 25
+
+
+def test_binding_constants_match_header(P):
+    """The binding's copies of the header's size limits are the header's values."""
+    src = open(os.path.join(ROOT, "include", "selbm.h")).read()
+    defines = dict(re.findall(r"#define\s+(SELBM_\w+)\s+(\d+)", src))
+    assert int(defines["SELBM_NOALLOC_MAX_ELEMS"]) == P.NOALLOC_MAX_ELEMS
+    assert int(defines["SELBM_TIMER_KINDS"]) == P.TIMER_KINDS

@@ -262,3 +262,35 @@ def test_stress_matches_oracle(P):
     pi_o = o.stress(f)[o.glo]
     pi_g = s.stress()
     assert rel(pi_g, pi_o) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_stress_with_force_field_mid_schedule(P, prec):
+    """selbm_stress with a per-node acceleration field on top of the body force, read at a time
+    where the field's factor A(t) = sin(2 pi t / period) is neither 0 nor 1 (t = 3 dt, period
+    8 dt: A = 0.707), so the field enters the collision target f_bar^eq = f^eq - dt/2 F** of the
+    stress with its current weight.  FP64 within 1e-9 of the oracle; FP32 deviations within
+    1e-4 of max |Pi| (the storage rounding of g, ~1e-9, against Pi ~ 5e-5)."""
+    mesh = W.box_mesh((4, 4), (0, 0), (1, 1), (True, False), walls={2: 1, 3: 1}, wall_velocity=[[0, 0]])
+    probe = OracleSELBM(mesh, "D2Q9", 8, nu=1.0, cfl=0.5)
+    nu = 0.2 * probe.dt / 3.0
+    G = 8 * nu * (0.1 / 3.0)
+    init = W.poiseuille_init(G, nu)
+    o, s = pair(P, mesh, "D2Q9", 8, nu, precision=prec, g=(G, 0.0, 0.0), init=init)
+    field = lambda x: np.stack([1e-2 * np.sin(2 * np.pi * x[:, 1]), 5e-3 * np.cos(2 * np.pi * x[:, 0])], 1)
+    period = 8 * o.dt
+    o.set_force_field(field(o.Xg), period, 1.0)
+    s.set_force_field(field, period, 1.0)
+    f = o.run(o.initial_state_from(init), 3)
+    s.init_from(init)
+    s.step(3)
+    assert abs(o.amplitude(o.time) - math.sqrt(0.5)) < 1e-9
+    s.set_state(np.ascontiguousarray(o.to_local(f)))
+    pi_o = o.stress(f)[o.glo]
+    pi_g = s.stress()
+    # the field's part of the collision target is a visible part of Pi (5e-3 of it: a factor
+    # A = 1 in place of 0.707 would be off by 1.6e-3, over both tolerances)
+    o2 = OracleSELBM(mesh, "D2Q9", 8, nu=nu, body_accel=(G, 0.0))
+    o2.time = o.time
+    assert rel(o2.stress(f)[o2.glo], pi_o) > 3e-3
+    assert rel(pi_g, pi_o) <= (1e-9 if prec == 0 else 1e-4)

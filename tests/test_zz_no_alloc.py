@@ -77,12 +77,37 @@ def test_noalloc_matches_diagnostics_twice(P, lattice, lat_id):
         _compare(got, s.diagnostics(), 1e-12)
 
 
+def test_noalloc_accepts_maximum(P):
+    """nelem == SELBM_NOALLOC_MAX_ELEMS is the largest size the scratch holds: accepted, and
+    the integrals of a state at rest (f = t_a rho, rho = 1 + 1e-3 k) with random weights
+    equal their direct sums, on two calls in a row."""
+    import torch
+    lib = P.load_library()
+    nelem, np_, Q = P.NOALLOC_MAX_ELEMS, 1, 9
+    rng = np.random.default_rng(3)
+    w = rng.uniform(0.5, 1.5, (nelem, np_))
+    t = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    for call in range(2):
+        rho = 1 + 1e-3 * (call + 1) * rng.standard_normal((nelem, np_))
+        f = torch.from_numpy(np.ascontiguousarray(t[:, None, None] * rho[None])).cuda()
+        wd = torch.from_numpy(np.ascontiguousarray(w)).cuda()
+        out = torch.full((6,), float("nan"), dtype=torch.float64, device="cuda")
+        rc = lib.selbm_integrals_noalloc(0, nelem, np_, C.c_void_p(f.data_ptr()), C.c_void_p(wd.data_ptr()), 1.0,
+                                         C.c_void_p(out.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == 0
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        mass = float((w * rho).sum())
+        assert abs(got[0] - mass) <= 1e-12 * mass
+        assert np.abs(got[1:5]).max() <= 1e-12 * mass and got[5] == 0.0
+
+
 def test_noalloc_rejects_oversize(P):
     import torch
     lib = P.load_library()
     buf = torch.zeros(16, dtype=torch.float64, device="cuda")
     p = C.c_void_p(buf.data_ptr())
-    too_many = 65536 + 1
+    too_many = P.NOALLOC_MAX_ELEMS + 1
     assert lib.selbm_integrals_noalloc(2, too_many, 1, p, p, 1.0, p, None) == -1
     assert lib.selbm_integrals_noalloc(2, 0, 1, p, p, 1.0, p, None) == -1
     assert lib.selbm_integrals_noalloc(7, 1, 1, p, p, 1.0, p, None) == -1
