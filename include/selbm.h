@@ -5,7 +5,9 @@
  *
  * One handle = one simulation on one GPU.  Every entry point returns an int
  * status (SELBM_OK = 0, negative = error; selbm_last_error() gives the text)
- * unless stated otherwise.  All work is enqueued on the CUDA stream given to
+ * unless stated otherwise.  The synchronising calls selbm_sync and
+ * selbm_diagnostics return the positive SELBM_OK_FALLBACK instead of SELBM_OK
+ * when the learned filter control's drift fallback is engaged.  All work is enqueued on the CUDA stream given to
  * selbm_create(); calls that return data to the host synchronise that stream.
  * Input arrays are copied; the caller keeps ownership of every pointer it
  * passes.  Output buffers are caller-owned and must be large enough.
@@ -28,6 +30,8 @@ extern "C" {
 typedef struct selbm selbm_t; /* opaque; owned by the library */
 
 enum {
+  SELBM_OK_FALLBACK = 1,    /* OK; the learned control's drift fallback has switched it off and the
+                               paper's fixed filter runs for the rest of the run */
   SELBM_OK = 0,
   SELBM_ERR_ARG = -1,       /* bad argument (NULL, size out of range, unsupported option) */
   SELBM_ERR_MESH = -2,      /* non-positive Jacobian, unmatched periodic nodes, bad tags */
@@ -77,6 +81,44 @@ typedef struct {
 } selbm_mesh;
 
 /*
+ * General curved, unstructured quad (dim 2) / hex (dim 3) mesh given by the GLL node
+ * coordinates of its isoparametric element maps (Sec. 2.2) and its face connectivity.
+ *  order            N_g, 1 <= N_g <= 14: the map of element e is the tensor-product Lagrange
+ *                   interpolant through xyz at the (N_g+1)^dim GLL nodes (N_g = 1: trilinear);
+ *                   the solver's own GLL nodes (order N of selbm_params) are interpolated
+ *                   from it, and the metrics are GLL derivatives of the interpolated map.
+ *  xyz[e][k][p]     coordinate k of node p = i + (N_g+1) j (+ (N_g+1)^2 l), r index fastest.
+ *  face_nbr[e][f]   element across face f (face ids as in selbm_mesh: 0 r=-1, 1 r=+1,
+ *                   2 s=-1, 3 s=+1, 4 t=-1, 5 t=+1), or -1 on the domain boundary.  Periodic
+ *                   faces name their partner (an element may be its own neighbour).
+ *  face_nbr_face[e][f]  the neighbour's face id.
+ *  face_orient[e][f]    how the face's nodes meet the neighbour's.  Face coordinates
+ *                   (a, b) of face f are its two tangential node indices in increasing axis
+ *                   order (faces 0, 1: (j, l); 2, 3: (i, l); 4, 5: (i, j); in 2D the single
+ *                   tangential index a).  Node (a, b) of face f of e is node (a', b') of face
+ *                   face_nbr_face of the neighbour, where (u, v) = (b, a) if bit 0 of the code
+ *                   is set, else (a, b); a' = N - u if bit 1 is set, else u; b' = N - v if bit
+ *                   2 is set, else v.  In 2D only bit 1 may be set.
+ *  face_bc[e][f]    0: interior, periodic or open face; k >= 1: wall k (flux bounce-back,
+ *                   Sec. 2.2.1) moving with wall_velocity[k-1].  May be NULL (no walls).
+ * Nodes are identified through the connectivity alone (no coordinate matching); the setup
+ * checks that the pairs are mutual and that matched nodes differ by one translation per face
+ * (zero inside the domain, a period across periodic faces), else SELBM_ERR_MESH.
+ */
+typedef struct {
+  int32_t dim;
+  int32_t nelem;
+  int32_t order;
+  const double *xyz;
+  const int32_t *face_nbr;
+  const int8_t *face_nbr_face;
+  const int8_t *face_orient;
+  const int32_t *face_bc;
+  int32_t nwalls;
+  const double *wall_velocity; /* [nwalls][dim] */
+} selbm_mesh_nodes;
+
+/*
  * Explicit modal filter (Sec. 2.4): sigma_k = 1 for k <= kc, else
  *  shape 0 (paper): 1 - gamma r^2;  shape 1: (1 - gamma)^(r^p);  r = (k-kc)/(N-kc).
  * Applied to every population, element by element, once per step after the
@@ -92,7 +134,7 @@ typedef struct {
 
 typedef struct {
   int32_t lattice;        /* SELBM_D2Q9 / D3Q19 / D3Q27 (dim must match the mesh) */
-  int32_t order;          /* polynomial order N, 2 <= N <= 12 */
+  int32_t order;          /* polynomial order N, 2 <= N <= 14 (3D: the element tile must fit in shared memory) */
   double nu;              /* kinematic viscosity; lambda = nu / cs^2, tau = lambda / dt */
   double dt;              /* > 0: time step; <= 0: dt = cfl * smallest GLL node spacing */
   double cfl;
@@ -109,6 +151,8 @@ typedef struct {
  * Errors: SELBM_ERR_ARG, SELBM_ERR_MESH, SELBM_ERR_CUDA; *out is NULL then.
  */
 int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_stream, selbm_t **out);
+/* The same for a mesh given by GLL node coordinates and face connectivity (selbm_mesh_nodes). */
+int selbm_create_nodes(const selbm_mesh_nodes *mesh, const selbm_params *params, void *cuda_stream, selbm_t **out);
 void selbm_destroy(selbm_t *h);
 /* Text of the last error on this handle (or of the last failed create when h is NULL). */
 const char *selbm_last_error(const selbm_t *h);
@@ -205,7 +249,8 @@ int selbm_set_force_field(selbm_t *h, const double *S, double period, double t_e
  * eps = 2 mu sum_i (d_i u_i)^2 - (2/3) mu (div u)^2 + mu sum_{i<j} (d_i u_j + d_j u_i)^2
  * (mu = rho0 nu; Sec. 3.4 with the square of the divergence term), quadrature over
  * element-local nodes with GLL derivatives, out[6] dt, out[7] time.
- * Returns SELBM_ERR_NONFINITE if the state holds NaN/Inf.
+ * Returns SELBM_ERR_NONFINITE if the state holds NaN/Inf, SELBM_OK_FALLBACK when the
+ * learned control's drift fallback is engaged.
  */
 int selbm_diagnostics(selbm_t *h, double out[8]);
 /*
@@ -296,6 +341,9 @@ int selbm_mlp_train(float *params, float *m, float *v, int32_t nin, int32_t orde
  * Errors as selbm_create (SELBM_ERR_ARG / SELBM_ERR_MESH), text in selbm_last_error(NULL).
  */
 int selbm_mesh_check(const selbm_mesh *mesh, int32_t lattice, int32_t order, int64_t out_i[6], double out_d[4]);
+/* The same dry run for a selbm_mesh_nodes mesh. */
+int selbm_mesh_check_nodes(const selbm_mesh_nodes *mesh, int32_t lattice, int32_t order, int64_t out_i[6],
+                           double out_d[4]);
 
 /*
  * Per-kernel device timers (tracing).  selbm_timers(h, 1) resets and starts
@@ -356,7 +404,8 @@ int selbm_timers_read(selbm_t *h, double ms[SELBM_TIMER_KINDS], int64_t n[SELBM_
 int selbm_integrals_noalloc(int32_t lattice, int32_t nelem, int32_t np, const double *f, const double *w,
                             double rho0, double *out, void *cuda_stream);
 
-/* Block until all work on the handle's stream is done; returns the first CUDA error seen. */
+/* Block until all work on the handle's stream is done; returns the first CUDA error seen,
+ * else SELBM_OK_FALLBACK when the learned control's drift fallback is engaged, else SELBM_OK. */
 int selbm_sync(selbm_t *h);
 
 #ifdef __cplusplus

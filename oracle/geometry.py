@@ -89,6 +89,84 @@ def element_nodes(mesh, xi):
     return X
 
 
+def element_nodes_from_map(mesh, xi):
+    """Node form of the mesh (Sec. 2.2, isoparametric elements): the element map is the
+    tensor-product Lagrange interpolant through the given coordinates at the GLL points of
+    order mesh.order; evaluated at the points xi -> X[E, Np, dim]."""
+    from . import gll
+    Ng, dim = int(mesh.order), mesh.dim
+    xg = gll.gll_nodes(Ng)
+    # l_j(x) = prod_{m != j} (x - xg_m) / (xg_j - xg_m)
+    Imat = np.ones((len(xi), Ng + 1))
+    for j in range(Ng + 1):
+        for m in range(Ng + 1):
+            if m != j:
+                Imat[:, j] *= (xi - xg[m]) / (xg[j] - xg[m])
+    n_to, n_from = len(xi), Ng + 1
+    E = mesh.nelem
+    X = np.zeros((E, n_to ** dim, dim))
+    for k in range(dim):
+        v = mesh.xyz[:, k, :].reshape((E,) + (n_from,) * dim)      # [E, (l), j, i]
+        for axis in range(dim):
+            ax = dim - axis                                         # array axis of reference axis
+            v = np.moveaxis(np.tensordot(v, Imat, axes=([ax], [1])), -1, ax)
+        X[:, :, k] = v.reshape(E, -1)
+    return X
+
+
+def face_local_nodes(N, dim, f):
+    """Local indices of the nodes of face f listed by face coordinates (a, b), a fastest: a and b
+    are the tangential node indices in increasing axis order."""
+    ijk = node_index_grid(N, dim)
+    axis, side = f // 2, f % 2
+    tang = [k for k in range(dim) if k != axis]
+    on = np.nonzero(ijk[:, axis] == (N if side else 0))[0]
+    a = ijk[on, tang[0]]
+    b = ijk[on, tang[1]] if dim == 3 else np.zeros_like(a)
+    order = np.lexsort((a, b))                # b slowest, a fastest
+    return on[order]
+
+
+def global_numbering_connectivity(mesh, N):
+    """Global numbering of the node form from its face connectivity alone -> glo[E, Np]: the
+    nodes (a, b) of face f of e and (a', b') of the neighbour's face are one node, with
+    (u, v) = (b, a) if bit 0 of the orientation code is set else (a, b), a' = N - u if bit 1,
+    b' = N - v if bit 2.  Ids in order of first appearance (element-major, node-minor)."""
+    dim, E = mesh.dim, mesh.nelem
+    n = N + 1
+    Np = n ** dim
+    parent = np.arange(E * Np)
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+    nb = n if dim == 3 else 1
+    for e in range(E):
+        for f in range(2 * dim):
+            e2 = int(mesh.face_nbr[e, f])
+            if e2 < 0:
+                continue
+            f2, code = int(mesh.face_nbr_face[e, f]), int(mesh.face_orient[e, f])
+            here, there = face_local_nodes(N, dim, f), face_local_nodes(N, dim, f2)
+            for b in range(nb):
+                for a in range(n):
+                    u, v = (b, a) if code & 1 else (a, b)
+                    a2 = N - u if code & 2 else u
+                    b2 = N - v if code & 4 else v
+                    r1 = find(e * Np + here[a + n * b])
+                    r2 = find(e2 * Np + there[a2 + n * b2])
+                    if r1 != r2:
+                        parent[max(r1, r2)] = min(r1, r2)
+    roots = np.array([find(q) for q in range(E * Np)])
+    _, first, inv = np.unique(roots, return_index=True, return_inverse=True)
+    order = np.argsort(first)
+    rank = np.empty_like(order)
+    rank[order] = np.arange(len(order))
+    return rank[inv].reshape(E, Np)
+
+
 # ----------------------------------------------------------------------------
 # geometric factors
 # ----------------------------------------------------------------------------

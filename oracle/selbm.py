@@ -44,12 +44,13 @@ class OracleSELBM:
         self.xi = gll.gll_nodes(N)
         self.w = gll.gll_weights(N, self.xi)
         self.D = gll.derivative_matrix(self.xi)
-        self.X = geo.element_nodes(mesh, self.xi)
+        node_form = hasattr(mesh, "xyz")               # GLL node coordinates + face connectivity
+        self.X = geo.element_nodes_from_map(mesh, self.xi) if node_form else geo.element_nodes(mesh, self.xi)
         self.E, self.Np = self.X.shape[0], self.X.shape[1]
         self.dxdr, self.J, self.drdx, self.wJ = geo.metrics(self.X, self.D, N, self.dim, self.w)
         if np.any(self.J <= 0):
             raise ValueError("non-positive Jacobian")
-        self.glo = geo.global_numbering(self.X, mesh)
+        self.glo = geo.global_numbering_connectivity(mesh, N) if node_form else geo.global_numbering(self.X, mesh)
         self.G = int(self.glo.max()) + 1
         self.mass = np.zeros(self.G)
         np.add.at(self.mass, self.glo.ravel(), self.wJ.ravel())

@@ -22,10 +22,11 @@ FP64, FP32DEV = 0, 1
 TIMER_KINDS = 5
 NOALLOC_MAX_ELEMS = 65536          # SELBM_NOALLOC_MAX_ELEMS of include/selbm.h
 TIMER_NAMES = ["stage1", "stage23", "assembly", "learned", "prologue"]
-ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_MESH", -3: "ERR_CUDA", -4: "ERR_NONFINITE", -5: "ERR_TIMEOUT", -6: "ERR_STATE"}
+OK_FALLBACK = 1                   # positive status: OK, the learned control's drift fallback is engaged
+ERRORS = {1: "OK_FALLBACK", 0: "OK", -1: "ERR_ARG", -2: "ERR_MESH", -3: "ERR_CUDA", -4: "ERR_NONFINITE", -5: "ERR_TIMEOUT", -6: "ERR_STATE"}
 
 # functions declared in include/selbm.h (checked by the ABI test)
-EXPORTS = ["selbm_create", "selbm_destroy", "selbm_last_error", "selbm_info", "selbm_lattice_table",
+EXPORTS = ["selbm_create", "selbm_create_nodes", "selbm_mesh_check_nodes", "selbm_destroy", "selbm_last_error", "selbm_info", "selbm_lattice_table",
            "selbm_node_coords", "selbm_init", "selbm_set_state", "selbm_get_state", "selbm_step",
            "selbm_moments", "selbm_stress", "selbm_set_filter", "selbm_set_body_force", "selbm_set_force_field", "selbm_set_time_scheme",
            "selbm_diagnostics", "selbm_sync",
@@ -46,6 +47,13 @@ class MeshC(C.Structure):
                 ("curved", C.POINTER(C.c_int32)), ("face_bc", C.POINTER(C.c_int32)),
                 ("period", C.POINTER(C.c_double)), ("origin", C.POINTER(C.c_double)),
                 ("nwalls", C.c_int32), ("wall_velocity", C.POINTER(C.c_double)), ("radius", C.c_double)]
+
+
+class MeshNodesC(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("nelem", C.c_int32), ("order", C.c_int32), ("xyz", C.POINTER(C.c_double)),
+                ("face_nbr", C.POINTER(C.c_int32)), ("face_nbr_face", C.POINTER(C.c_int8)),
+                ("face_orient", C.POINTER(C.c_int8)), ("face_bc", C.POINTER(C.c_int32)), ("nwalls", C.c_int32),
+                ("wall_velocity", C.POINTER(C.c_double))]
 
 
 class FilterC(C.Structure):
@@ -71,6 +79,8 @@ def load_library(path: str = LIB_PATH):
     lib = C.CDLL(path)
     P, I, D, I64 = C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_int64
     lib.selbm_create.argtypes = [C.POINTER(MeshC), C.POINTER(ParamsC), P, C.POINTER(P)]
+    lib.selbm_create_nodes.argtypes = [C.POINTER(MeshNodesC), C.POINTER(ParamsC), P, C.POINTER(P)]
+    lib.selbm_mesh_check_nodes.argtypes = [C.POINTER(MeshNodesC), C.c_int32, C.c_int32, C.POINTER(C.c_int64), D]
     lib.selbm_destroy.argtypes = [P]
     lib.selbm_destroy.restype = None
     lib.selbm_last_error.argtypes = [P]
@@ -149,14 +159,35 @@ def mesh_struct(mesh):
     return m, keep
 
 
+def mesh_nodes_struct(mesh):
+    """(MeshNodesC, keep-alive list) for a workloads.NodeMeshSpec-like object."""
+    dim = int(mesh.dim)
+    keep = [np.ascontiguousarray(mesh.xyz, np.float64), np.ascontiguousarray(mesh.face_nbr, np.int32),
+            np.ascontiguousarray(mesh.face_nbr_face, np.int8), np.ascontiguousarray(mesh.face_orient, np.int8),
+            np.ascontiguousarray(mesh.bc, np.int32),
+            np.ascontiguousarray(np.asarray(mesh.wall_velocity, np.float64).reshape(-1, dim))]
+    x, nb, nf, no, bc, wv = keep
+    m = MeshNodesC(dim, int(x.shape[0]), int(mesh.order), _dptr(x), nb.ctypes.data_as(C.POINTER(C.c_int32)),
+                   nf.ctypes.data_as(C.POINTER(C.c_int8)), no.ctypes.data_as(C.POINTER(C.c_int8)),
+                   bc.ctypes.data_as(C.POINTER(C.c_int32)), int(wv.shape[0]), _dptr(wv) if wv.size else None)
+    return m, keep
+
+
+def _is_node_mesh(mesh):
+    return hasattr(mesh, "xyz") and hasattr(mesh, "face_nbr")
+
+
 def mesh_check(mesh, lattice, order):
-    """Host-only dry run of the setup: dict of sizes and integrals (no GPU needed)."""
+    """Host-only dry run of the setup: dict of sizes and integrals (no GPU needed).  ``mesh`` is
+    a corner mesh (workloads.MeshSpec) or a node mesh (workloads.NodeMeshSpec)."""
     lib = load_library()
-    m, keep = mesh_struct(mesh)
+    node = _is_node_mesh(mesh)
+    m, keep = mesh_nodes_struct(mesh) if node else mesh_struct(mesh)
     ii = (C.c_int64 * 6)()
     dd = (C.c_double * 4)()
     lat = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
-    rc = lib.selbm_mesh_check(C.byref(m), lat, int(order), ii, dd)
+    check = lib.selbm_mesh_check_nodes if node else lib.selbm_mesh_check
+    rc = check(C.byref(m), lat, int(order), ii, dd)
     if rc != 0:
         raise SelbmError(rc, lib.selbm_last_error(None).decode())
     del keep
@@ -166,13 +197,16 @@ def mesh_check(mesh, lattice, order):
 
 class SELBM:
     """One simulation handle.  ``mesh`` is a ``workloads.MeshSpec``-like object
-    (dim, verts, curved, bc, period, origin, wall_velocity, radius)."""
+    (dim, verts, curved, bc, period, origin, wall_velocity, radius) or a
+    ``workloads.NodeMeshSpec``-like one (dim, order, xyz, face_nbr, face_nbr_face,
+    face_orient, bc, wall_velocity)."""
 
     def __init__(self, mesh, lattice, order, nu, cfl=0.5, dt=0.0, rho0=1.0, precision=FP64,
                  filt=None, body_accel=(0.0, 0.0, 0.0), stream=None):
         self.lib = load_library()
         dim = int(mesh.dim)
-        m, self._keep = mesh_struct(mesh)
+        node = _is_node_mesh(mesh)
+        m, self._keep = mesh_nodes_struct(mesh) if node else mesh_struct(mesh)
         g = list(body_accel) + [0.0] * (3 - len(body_accel))
         lat = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
         p = ParamsC(lat, int(order), float(nu), float(dt), float(cfl), float(rho0), int(precision),
@@ -185,7 +219,8 @@ class SELBM:
                 stream = 0
         self.stream = stream
         h = C.c_void_p()
-        rc = self.lib.selbm_create(C.byref(m), C.byref(p), C.c_void_p(stream), C.byref(h))
+        create = self.lib.selbm_create_nodes if node else self.lib.selbm_create
+        rc = create(C.byref(m), C.byref(p), C.c_void_p(stream), C.byref(h))
         if rc != 0:
             raise SelbmError(rc, self.lib.selbm_last_error(None).decode())
         self.h = h
@@ -193,7 +228,8 @@ class SELBM:
         self._info()
 
     def _check(self, rc):
-        if rc != 0:
+        """Raise on a negative status; 0 and the positive OK_FALLBACK pass through."""
+        if rc < 0:
             raise SelbmError(rc, self.lib.selbm_last_error(self.h).decode())
         return rc
 
@@ -299,8 +335,10 @@ class SELBM:
         self._check(self.lib.selbm_set_force_field(self.h, None, 0.0, 0.0))
 
     def diagnostics(self):
+        """[mass, momentum x3, KE, dissipation, dt, t]; self.fallback_engaged records whether the
+        call returned OK_FALLBACK."""
         out = np.zeros(8)
-        self._check(self.lib.selbm_diagnostics(self.h, _dptr(out)))
+        self.fallback_engaged = self._check(self.lib.selbm_diagnostics(self.h, _dptr(out))) == OK_FALLBACK
         return out
 
     def wall_stress(self, direction):
@@ -330,7 +368,8 @@ class SELBM:
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(TIMER_NAMES)}
 
     def sync(self):
-        self._check(self.lib.selbm_sync(self.h))
+        """Wait for the handle's stream; returns OK (0) or OK_FALLBACK (1)."""
+        return self._check(self.lib.selbm_sync(self.h))
 
     # ------------------------------------------------------- learned control
     def set_learned_filter(self, params, lo, hi, mass_bound=1e-6, ke_bound=0.0):

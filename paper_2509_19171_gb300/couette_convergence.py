@@ -29,7 +29,7 @@ def series(y, t, u_top, nu, terms=400):
                         * np.exp(-nu * (n * math.pi) ** 2 * t)).sum(0)
 
 
-def run(orders=(4, 6, 8, 10, 12), schemes=(0, 1, 2), ne=6, Re=2000.0, Ma=0.05, t_over_t0=40.0, cfl=0.5):
+def run(orders=(4, 6, 8, 10, 12, 14), schemes=(0, 1, 2), ne=6, Re=2000.0, Ma=0.05, t_over_t0=40.0, cfl=0.5):
     import workloads as W
     u_top = Ma / math.sqrt(3.0)
     nu = u_top / Re
@@ -62,7 +62,7 @@ def run(orders=(4, 6, 8, 10, 12), schemes=(0, 1, 2), ne=6, Re=2000.0, Ma=0.05, t
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default="couette.json")
-    ap.add_argument("--orders", default="4,6,8,10,12")
+    ap.add_argument("--orders", default="4,6,8,10,12,14")
     ap.add_argument("--schemes", default="0,1,2")
     args = ap.parse_args()
     res = run(orders=tuple(int(x) for x in args.orders.split(",")),

@@ -350,8 +350,11 @@ cudaError_t enqueue_step_split(selbm *h, bool apply_filter) {
     if (e) return e;
     h->mark_end(4, t0);
   }
-  const Real A[3] = {Real(0), Real(0.75), Real(1.0 / 3.0)};
+  // Shu-Osher weights with A = 1 - B formed in the working precision: A + B = 1 exactly, so a
+  // stage combination A f0 + B f' of the deviations carries no systematic scale error (with
+  // A = fl(1/3), B = fl(2/3) in FP32 the sum is 1 + 3e-8 and the state drifts by that every step)
   const Real B[3] = {Real(1), Real(0.25), Real(2.0 / 3.0)};
+  const Real A[3] = {Real(0), Real(1) - B[1], Real(1) - B[2]};
   const Real *fin[3] = {F0, FA, F2};   // f^{s-1}: stage 1 advects f^0
   Real *fout[3] = {FA, F2, FA};
   for (int s = 0; s < 3; ++s) {
@@ -453,8 +456,11 @@ cudaError_t enqueue_step(selbm *h, bool apply_filter) {
   KParams<Real> p = base_params<Real>(h);
   if (h->use_split) return enqueue_step_split<Real>(h, apply_filter);
   Real *FA = (Real *)h->FA, *F0 = (Real *)h->F0, *F2 = (Real *)h->F2;
-  const Real A[3] = {Real(0), Real(0.75), Real(1.0 / 3.0)};
+  // Shu-Osher weights with A = 1 - B formed in the working precision: A + B = 1 exactly, so a
+  // stage combination A f0 + B f' of the deviations carries no systematic scale error (with
+  // A = fl(1/3), B = fl(2/3) in FP32 the sum is 1 + 3e-8 and the state drifts by that every step)
   const Real B[3] = {Real(1), Real(0.25), Real(2.0 / 3.0)};
+  const Real A[3] = {Real(0), Real(1) - B[1], Real(1) - B[2]};
   const Real *fin[3] = {FA, FA, F2};   // element-kernel input f^{s-1} (stage 1: f^3 of the last step)
   Real *fout[3] = {FA, F2, FA};
   cudaError_t e;
@@ -519,6 +525,16 @@ int set_filter_internal(selbm *h, const selbm_filter &f) {
   return SELBM_OK;
 }
 
+// SELBM_OK_FALLBACK when the learned control is on and its drift fallback has tripped (reads
+// the device flag: the caller has synchronised the stream), else SELBM_OK
+int fallback_status(selbm *h) {
+  if (!h->learned) return SELBM_OK;
+  int flag = 0;
+  cudaError_t e = cudaMemcpy(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return h->cuda_fail(e, "fallback flag");
+  return flag ? SELBM_OK_FALLBACK : SELBM_OK;
+}
+
 int ensure_io(selbm *h, size_t bytes) {
   if (h->io_bytes >= bytes) return SELBM_OK;
   if (h->d_io) cudaFree(h->d_io);
@@ -531,12 +547,11 @@ int ensure_io(selbm *h, size_t bytes) {
 
 }  // namespace
 
-// ===========================================================================
-extern "C" {
-
-int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_stream, selbm_t **out) {
+// shared body of selbm_create / selbm_create_nodes: `setup` fills the handle's Setup
+template <typename SetupFn>
+static int create_impl(SetupFn setup, const selbm_params *params, void *cuda_stream, selbm_t **out) {
   if (out) *out = nullptr;
-  if (!mesh || !params || !out) { g_create_error = "NULL argument"; return SELBM_ERR_ARG; }
+  if (!params || !out) { g_create_error = "NULL argument"; return SELBM_ERR_ARG; }
   if (params->precision != SELBM_FP64 && params->precision != SELBM_FP32DEV) { g_create_error = "unknown precision"; return SELBM_ERR_ARG; }
   if (!(params->nu > 0.0)) { g_create_error = "nu must be positive"; return SELBM_ERR_ARG; }
   selbm *h = new selbm();
@@ -552,7 +567,7 @@ int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_
     h->graph_enabled = !(ng && ng[0] == '1');
   }
   std::string err;
-  int rc = build_setup(*mesh, params->lattice, params->order, &h->S, &err);
+  int rc = setup(&h->S, &err);
   if (rc != SELBM_OK) { g_create_error = err; delete h; return rc; }
   Setup &S = h->S;
   h->Q = S.lat.Q;
@@ -589,6 +604,37 @@ int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_
   if (rc != SELBM_OK) { g_create_error = h->err; selbm_destroy(h); return rc; }
   *out = h;
   return SELBM_OK;
+}
+
+static int mesh_check_out(const Setup &S, int64_t out_i[6], double out_d[4]) {
+  if (out_i) {
+    out_i[0] = S.E; out_i[1] = S.Np; out_i[2] = S.lat.Q; out_i[3] = S.G; out_i[4] = S.Gb; out_i[5] = S.affine ? 1 : 0;
+  }
+  if (out_d) {
+    double m = 0.0, ws = 0.0;
+    for (double v : S.mass) m += v;
+    for (const WallNode &w : S.walls) ws += w.wsJs;
+    out_d[0] = S.min_spacing; out_d[1] = m; out_d[2] = (double)S.walls.size(); out_d[3] = ws;
+  }
+  return SELBM_OK;
+}
+
+// ===========================================================================
+extern "C" {
+
+int selbm_create(const selbm_mesh *mesh, const selbm_params *params, void *cuda_stream, selbm_t **out) {
+  if (out) *out = nullptr;
+  if (!mesh) { g_create_error = "NULL argument"; return SELBM_ERR_ARG; }
+  return create_impl([&](Setup *S, std::string *err) { return build_setup(*mesh, params->lattice, params->order, S, err); },
+                     params, cuda_stream, out);
+}
+
+int selbm_create_nodes(const selbm_mesh_nodes *mesh, const selbm_params *params, void *cuda_stream, selbm_t **out) {
+  if (out) *out = nullptr;
+  if (!mesh) { g_create_error = "NULL argument"; return SELBM_ERR_ARG; }
+  return create_impl(
+      [&](Setup *S, std::string *err) { return build_setup_nodes(*mesh, params->lattice, params->order, S, err); },
+      params, cuda_stream, out);
 }
 
 void selbm_destroy(selbm_t *h) {
@@ -938,7 +984,7 @@ int selbm_diagnostics(selbm_t *h, double out[8]) {
   for (int k = 0; k < 3; ++k) out[1 + k] = tmp[1 + k];
   out[4] = tmp[4]; out[5] = tmp[6]; out[6] = h->dt; out[7] = h->time;
   if (tmp[5] > 0) return h->fail(SELBM_ERR_NONFINITE, "state holds non-finite values");
-  return SELBM_OK;
+  return fallback_status(h);
 }
 
 int selbm_wall_stress(selbm_t *h, const double dir[3], double *tau) {
@@ -1029,17 +1075,19 @@ int selbm_mesh_check(const selbm_mesh *mesh, int32_t lattice, int32_t order, int
   std::string err;
   int rc = build_setup(*mesh, lattice, order, &S, &err);
   if (rc != SELBM_OK) { g_create_error = err; return rc; }
-  if (out_i) {
-    out_i[0] = S.E; out_i[1] = S.Np; out_i[2] = S.lat.Q; out_i[3] = S.G; out_i[4] = S.Gb; out_i[5] = S.affine ? 1 : 0;
-  }
-  if (out_d) {
-    double m = 0.0, ws = 0.0;
-    for (double v : S.mass) m += v;
-    for (const WallNode &w : S.walls) ws += w.wsJs;
-    out_d[0] = S.min_spacing; out_d[1] = m; out_d[2] = (double)S.walls.size(); out_d[3] = ws;
-  }
-  return SELBM_OK;
+  return mesh_check_out(S, out_i, out_d);
 }
+
+int selbm_mesh_check_nodes(const selbm_mesh_nodes *mesh, int32_t lattice, int32_t order, int64_t out_i[6],
+                           double out_d[4]) {
+  if (!mesh) { g_create_error = "NULL mesh"; return SELBM_ERR_ARG; }
+  Setup S;
+  std::string err;
+  int rc = build_setup_nodes(*mesh, lattice, order, &S, &err);
+  if (rc != SELBM_OK) { g_create_error = err; return rc; }
+  return mesh_check_out(S, out_i, out_d);
+}
+
 
 int selbm_timers(selbm_t *h, int enable) {
   if (!h) return SELBM_ERR_ARG;
@@ -1244,7 +1292,7 @@ int selbm_sync(selbm_t *h) {
   if (!h) return SELBM_ERR_ARG;
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "sync");
-  return SELBM_OK;
+  return fallback_status(h);
 }
 
 }  // extern "C"

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "selbm_learn.cuh"
+#include "selbm_setup.h"
 #include "selbm_lattice.cuh"
 
 namespace slb {
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(256) control_kernel(const ControlArgs<Real> c)
       const int fld = t / nl, L = t - fld * nl;
       const int base = axis == 0 ? L * n : (axis == 1 ? (L % n) + n * n * (L / n) : L);
       Real *row = q + fld * Np + base;
-      Real v[13], o[13];
+      Real v[kMaxN + 1], o[kMaxN + 1];
       for (int k = 0; k < n; ++k) v[k] = row[k * stride];
       for (int m = 0; m < n; ++m) {
         Real s = 0;
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(256) control_kernel(const ControlArgs<Real> c)
       const int a = t / nl, L = t - a * nl;
       const int base = axis == 0 ? L * n : (axis == 1 ? (L % n) + n * n * (L / n) : L);
       Real *row = sf + a * Np + base;
-      Real v[13], o[13];
+      Real v[kMaxN + 1], o[kMaxN + 1];
       for (int k = 0; k < n; ++k) v[k] = row[k * stride];
       for (int m = 0; m < n; ++m) {
         Real s = 0;

@@ -253,15 +253,184 @@ struct KeyHash {
   }
 };
 
-int build_setup(const selbm_mesh &mesh, int lattice, int N, Setup *S, std::string *err) {
-  const int dim = mesh.dim;
+// ---------------------------------------------------------------------------
+// node-coordinate mesh form (Sec. 2.2 isoparametric elements): the element map through the
+// given GLL nodes, interpolated to the solver's nodes; nodes identified by face connectivity
+// ---------------------------------------------------------------------------
+// local index of node (a, b) of face f (face coordinates: tangential indices in increasing
+// axis order), order N
+static int face_node(int dim, int N, int f, int a, int b) {
+  const int n = N + 1, axis = f / 2, fixed = (f % 2) ? N : 0;
+  int idx[3] = {0, 0, 0};
+  idx[axis] = fixed;
+  if (dim == 2) {
+    idx[1 - axis] = a;
+    return idx[0] + n * idx[1];
+  }
+  const int t0 = axis == 0 ? 1 : 0, t1 = axis == 2 ? 1 : 2;
+  idx[t0] = a;
+  idx[t1] = b;
+  return idx[0] + n * idx[1] + n * n * idx[2];
+}
+
+// face coordinates on the neighbour's face for orientation code `code`
+static void orient_map(int code, int N, int a, int b, int *a2, int *b2) {
+  int u = (code & 1) ? b : a, v = (code & 1) ? a : b;
+  *a2 = (code & 2) ? N - u : u;
+  *b2 = (code & 4) ? N - v : v;
+}
+
+// x at the solver's GLL nodes (order N) from the coordinates at the GLL nodes of order N_g:
+// X[e][p][k] = sum over the given nodes of the tensor-product Lagrange basis at node p
+static int nodes_to_gll(const selbm_mesh_nodes &m, int N, const GLL &g, std::vector<double> *X, std::string *err) {
+  (void)g;
+  const int dim = m.dim, E = m.nelem, Ng = m.order;
+  if (!m.xyz) { *err = "mesh xyz is NULL"; return SELBM_ERR_ARG; }
+  if (Ng < 1 || Ng > kMaxN) { *err = "mesh order out of range [1, 14]"; return SELBM_ERR_ARG; }
+  const int ng = Ng + 1, n = N + 1;
+  int Npg = 1, Np = 1;
+  for (int k = 0; k < dim; ++k) { Npg *= ng; Np *= n; }
+  std::vector<double> I;
+  build_interp(Ng, N, &I);                                   // [n][ng]
+  X->assign((size_t)E * Np * dim, 0.0);
+  std::vector<double> a, b;
+  for (int e = 0; e < E; ++e)
+    for (int c = 0; c < dim; ++c) {
+      const double *in = m.xyz + ((size_t)e * dim + c) * Npg;
+      for (int v = 0; v < Npg; ++v)
+        if (!std::isfinite(in[v])) { *err = "mesh xyz holds a non-finite value"; return SELBM_ERR_MESH; }
+      // axis by axis: sizes (ng, ng, ng) -> (n, ng, ng) -> (n, n, ng) -> (n, n, n)
+      a.assign(in, in + Npg);
+      int s0 = ng, s1 = ng, s2 = dim == 3 ? ng : 1;
+      for (int axis = 0; axis < dim; ++axis) {
+        int d[3] = {s0, s1, s2};
+        int o[3] = {s0, s1, s2};
+        o[axis] = n;
+        b.assign((size_t)o[0] * o[1] * o[2], 0.0);
+        for (int k = 0; k < o[2]; ++k)
+          for (int j = 0; j < o[1]; ++j)
+            for (int i = 0; i < o[0]; ++i) {
+              const int out_i[3] = {i, j, k};
+              double acc = 0.0;
+              for (int m2 = 0; m2 < ng; ++m2) {
+                int src[3] = {i, j, k};
+                src[axis] = m2;
+                acc += I[out_i[axis] * ng + m2] * a[src[0] + d[0] * (src[1] + d[1] * src[2])];
+              }
+              b[i + o[0] * (j + o[1] * k)] = acc;
+            }
+        a.swap(b);
+        s0 = o[0]; s1 = o[1]; s2 = o[2];
+      }
+      for (int p = 0; p < Np; ++p) (*X)[((size_t)e * Np + p) * dim + c] = a[p];
+    }
+  return SELBM_OK;
+}
+
+static int uf_find(std::vector<int64_t> &par, int64_t x) {
+  while (par[x] != x) {
+    par[x] = par[par[x]];
+    x = par[x];
+  }
+  return (int)x;
+}
+
+// global numbering from face connectivity: the nodes of matched faces are joined (union-find),
+// each class numbered in order of its first local copy; checks mutual pairs and that matched
+// nodes differ by one translation per face
+static int number_by_connectivity(const selbm_mesh_nodes &m, int N, Setup *S, int32_t *G, std::string *err) {
+  const int dim = m.dim, E = m.nelem, nf = 2 * dim, n = N + 1;
+  int Np = 1;
+  for (int k = 0; k < dim; ++k) Np *= n;
+  if (!m.face_nbr || !m.face_nbr_face || !m.face_orient) { *err = "face connectivity arrays are NULL"; return SELBM_ERR_ARG; }
+  double scale = 0.0;
+  {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (size_t q = 0; q < (size_t)E * Np; ++q)
+      for (int k = 0; k < dim; ++k) {
+        lo[k] = std::min(lo[k], S->X[q * dim + k]);
+        hi[k] = std::max(hi[k], S->X[q * dim + k]);
+      }
+    for (int k = 0; k < dim; ++k) scale = std::max(scale, hi[k] - lo[k]);
+  }
+  const double tol = 1e-9 * scale;
+  std::vector<int64_t> par((size_t)E * Np);
+  for (size_t q = 0; q < par.size(); ++q) par[q] = (int64_t)q;
+  const int nb = dim == 3 ? n : 1;                   // second face coordinate range
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < nf; ++f) {
+      const int e2 = m.face_nbr[(size_t)e * nf + f];
+      if (e2 < 0) continue;
+      if (e2 >= E) { *err = "face_nbr names an element beyond nelem"; return SELBM_ERR_MESH; }
+      const int f2 = m.face_nbr_face[(size_t)e * nf + f], code = m.face_orient[(size_t)e * nf + f];
+      if (f2 < 0 || f2 >= nf) { *err = "face_nbr_face out of range"; return SELBM_ERR_MESH; }
+      if (code < 0 || code > 7 || (dim == 2 && (code & 5))) { *err = "face_orient out of range"; return SELBM_ERR_MESH; }
+      if (e2 == e && f2 == f) { *err = "a face is its own neighbour"; return SELBM_ERR_MESH; }
+      if (m.face_nbr[(size_t)e2 * nf + f2] != e || m.face_nbr_face[(size_t)e2 * nf + f2] != f) {
+        *err = "face connectivity is not mutual";
+        return SELBM_ERR_MESH;
+      }
+      if (m.face_bc && m.face_bc[(size_t)e * nf + f] > 0) { *err = "a wall face has a neighbour"; return SELBM_ERR_MESH; }
+      const int code2 = m.face_orient[(size_t)e2 * nf + f2];
+      double shift[3] = {0, 0, 0};
+      for (int b = 0; b < nb; ++b)
+        for (int a = 0; a < n; ++a) {
+          int a2, b2, a3, b3;
+          orient_map(code, N, a, b, &a2, &b2);
+          if (dim == 2) b2 = 0;
+          orient_map(code2, N, a2, b2, &a3, &b3);   // back from the neighbour's side
+          if (dim == 2) b3 = 0;
+          if (a3 != a || b3 != b) { *err = "face orientations of a face pair are not inverse"; return SELBM_ERR_MESH; }
+          const size_t q = (size_t)e * Np + face_node(dim, N, f, a, b);
+          const size_t q2 = (size_t)e2 * Np + face_node(dim, N, f2, a2, b2);
+          for (int k = 0; k < dim; ++k) {
+            const double dk = S->X[q2 * dim + k] - S->X[q * dim + k];
+            if (a == 0 && b == 0) shift[k] = dk;
+            else if (std::fabs(dk - shift[k]) > tol) {
+              *err = "matched face nodes do not coincide up to one translation (orientation?)";
+              return SELBM_ERR_MESH;
+            }
+          }
+          const int r1 = uf_find(par, (int64_t)q), r2 = uf_find(par, (int64_t)q2);
+          if (r1 != r2) par[std::max(r1, r2)] = std::min(r1, r2);
+        }
+    }
+  S->l2g.assign((size_t)E * Np, -1);
+  S->owner.assign((size_t)E * Np, 0);
+  std::vector<int32_t> id((size_t)E * Np, -1);
+  int32_t g = 0;
+  for (size_t q = 0; q < (size_t)E * Np; ++q) {
+    const int r = uf_find(par, (int64_t)q);
+    if (id[r] < 0) {
+      id[r] = g++;
+      S->owner[q] = 1;
+    }
+    S->l2g[q] = id[r];
+  }
+  *G = g;
+  return SELBM_OK;
+}
+
+// The two mesh forms of the ABI: element corners (+ arcs, periods) or GLL node coordinates with
+// face connectivity.  Everything after the coordinates and the global numbering is shared.
+struct MeshInput {
+  int dim = 0, nelem = 0;
+  const selbm_mesh *corners = nullptr;
+  const selbm_mesh_nodes *nodes = nullptr;
+  const int32_t *face_bc = nullptr;
+  int nwalls = 0;
+  const double *wall_velocity = nullptr;
+};
+
+static int build_setup_impl(const MeshInput &mi, int lattice, int N, Setup *S, std::string *err) {
+  const int dim = mi.dim;
   if (dim != 2 && dim != 3) { *err = "mesh.dim must be 2 or 3"; return SELBM_ERR_ARG; }
-  if (mesh.nelem <= 0 || !mesh.verts) { *err = "mesh has no elements"; return SELBM_ERR_ARG; }
-  if (N < 2 || N > kMaxN) { *err = "order N out of range [2, 12]"; return SELBM_ERR_ARG; }
+  if (mi.nelem <= 0) { *err = "mesh has no elements"; return SELBM_ERR_ARG; }
+  if (N < 2 || N > kMaxN) { *err = "order N out of range [2, 14]"; return SELBM_ERR_ARG; }
   if (!build_lattice(lattice, &S->lat)) { *err = "unknown lattice"; return SELBM_ERR_ARG; }
   if (S->lat.dim != dim) { *err = "lattice dimension does not match the mesh"; return SELBM_ERR_ARG; }
-  S->dim = dim; S->E = mesh.nelem; S->N = N; S->n1 = N + 1;
-  const int n = N + 1, E = mesh.nelem;
+  S->dim = dim; S->E = mi.nelem; S->N = N; S->n1 = N + 1;
+  const int n = N + 1, E = mi.nelem;
   int Np = 1, Nint = 1;
   for (int k = 0; k < dim; ++k) { Np *= n; Nint *= (N - 1); }
   S->Np = Np; S->Nb = Np - Nint;
@@ -285,23 +454,29 @@ int build_setup(const selbm_mesh &mesh, int lattice, int N, Setup *S, std::strin
 
   // node coordinates
   S->X.assign((size_t)E * Np * dim, 0.0);
-  for (int e = 0; e < E; ++e) {
-    const double *C = mesh.verts + (size_t)e * (1 << dim) * dim;
-    int cv[4] = {0, 0, 0, 0};
-    if (mesh.curved)
-      for (int f = 0; f < 4; ++f) cv[f] = mesh.curved[(size_t)e * 2 * dim + f] != 0;
-    for (int p = 0; p < Np; ++p) {
-      double r = xi[ijk[3 * p]], s = xi[ijk[3 * p + 1]];
-      double *out = &S->X[((size_t)e * Np + p) * dim];
-      if (dim == 2) {
-        quad_point(C, cv, r, s, mesh.radius, 2, out);
-      } else {
-        double t = xi[ijk[3 * p + 2]], lo[3], hi[3];
-        quad_point(C, cv, r, s, mesh.radius, 3, lo);
-        quad_point(C + 4 * 3, cv, r, s, mesh.radius, 3, hi);
-        for (int k = 0; k < 3; ++k) out[k] = 0.5 * (1 - t) * lo[k] + 0.5 * (1 + t) * hi[k];
+  if (mi.corners) {
+    const selbm_mesh &mesh = *mi.corners;
+    for (int e = 0; e < E; ++e) {
+      const double *C = mesh.verts + (size_t)e * (1 << dim) * dim;
+      int cv[4] = {0, 0, 0, 0};
+      if (mesh.curved)
+        for (int f = 0; f < 4; ++f) cv[f] = mesh.curved[(size_t)e * 2 * dim + f] != 0;
+      for (int p = 0; p < Np; ++p) {
+        double r = xi[ijk[3 * p]], s = xi[ijk[3 * p + 1]];
+        double *out = &S->X[((size_t)e * Np + p) * dim];
+        if (dim == 2) {
+          quad_point(C, cv, r, s, mesh.radius, 2, out);
+        } else {
+          double t = xi[ijk[3 * p + 2]], lo[3], hi[3];
+          quad_point(C, cv, r, s, mesh.radius, 3, lo);
+          quad_point(C + 4 * 3, cv, r, s, mesh.radius, 3, hi);
+          for (int k = 0; k < 3; ++k) out[k] = 0.5 * (1 - t) * lo[k] + 0.5 * (1 + t) * hi[k];
+        }
       }
     }
+  } else {
+    int rc = nodes_to_gll(*mi.nodes, N, S->gll, &S->X, err);
+    if (rc != SELBM_OK) return rc;
   }
 
   // metrics: dx_k/dr_l = D along axis l applied to x_k; inverse; J; wJ
@@ -367,61 +542,67 @@ int build_setup(const selbm_mesh &mesh, int lattice, int N, Setup *S, std::strin
     S->el_J[e] = J0;
   }
 
-  // global numbering: quantised, periodically wrapped coordinates
-  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-  for (size_t q = 0; q < (size_t)E * Np; ++q)
-    for (int k = 0; k < dim; ++k) { lo[k] = std::min(lo[k], S->X[q * dim + k]); hi[k] = std::max(hi[k], S->X[q * dim + k]); }
-  double scale = 0.0;
-  for (int k = 0; k < dim; ++k) scale = std::max(scale, hi[k] - lo[k]);
-  const double quantum = 1e-7 * scale;
-  std::unordered_map<Key, int32_t, KeyHash> map;
-  map.reserve((size_t)E * Np);
-  S->l2g.assign((size_t)E * Np, -1);
-  S->owner.assign((size_t)E * Np, 0);
+  // global numbering: coordinates (corner form) or face connectivity (node form)
   int32_t G = 0;
-  for (size_t q = 0; q < (size_t)E * Np; ++q) {
-    double y[3] = {0, 0, 0};
-    for (int k = 0; k < dim; ++k) {
-      y[k] = S->X[q * dim + k];
-      double L = mesh.period ? mesh.period[k] : 0.0;
-      if (L > 0.0) {
-        double o = mesh.origin ? mesh.origin[k] : 0.0;
-        double v = std::fmod(y[k] - o, L);
-        if (v < 0) v += L;
-        if (L - v < 1e-7 * scale) v -= L;
-        y[k] = v;
+  if (mi.nodes) {
+    int rc = number_by_connectivity(*mi.nodes, N, S, &G, err);
+    if (rc != SELBM_OK) return rc;
+  } else {
+    const selbm_mesh &mesh = *mi.corners;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (size_t q = 0; q < (size_t)E * Np; ++q)
+      for (int k = 0; k < dim; ++k) { lo[k] = std::min(lo[k], S->X[q * dim + k]); hi[k] = std::max(hi[k], S->X[q * dim + k]); }
+    double scale = 0.0;
+    for (int k = 0; k < dim; ++k) scale = std::max(scale, hi[k] - lo[k]);
+    const double quantum = 1e-7 * scale;
+    std::unordered_map<Key, int32_t, KeyHash> map;
+    map.reserve((size_t)E * Np);
+    S->l2g.assign((size_t)E * Np, -1);
+    S->owner.assign((size_t)E * Np, 0);
+    for (size_t q = 0; q < (size_t)E * Np; ++q) {
+      double y[3] = {0, 0, 0};
+      for (int k = 0; k < dim; ++k) {
+        y[k] = S->X[q * dim + k];
+        double L = mesh.period ? mesh.period[k] : 0.0;
+        if (L > 0.0) {
+          double o = mesh.origin ? mesh.origin[k] : 0.0;
+          double v = std::fmod(y[k] - o, L);
+          if (v < 0) v += L;
+          if (L - v < 1e-7 * scale) v -= L;
+          y[k] = v;
+        }
       }
-    }
-    // candidate keys: nearest cell, plus the other side for coordinates close to a cell edge
-    int64_t base[3], alt[3];
-    bool amb[3] = {false, false, false};
-    for (int k = 0; k < 3; ++k) {
-      double u = y[k] / quantum;
-      base[k] = (int64_t)std::llround(u);
-      double fr = u - std::floor(u);
-      alt[k] = fr < 0.5 ? base[k] + 1 : base[k] - 1;
-      amb[k] = std::fabs(fr - 0.5) < 1e-3;
-    }
-    int32_t found = -1;
-    for (int m = 0; m < 8 && found < 0; ++m) {
-      Key key;
-      bool ok = true;
+      // candidate keys: nearest cell, plus the other side for coordinates close to a cell edge
+      int64_t base[3], alt[3];
+      bool amb[3] = {false, false, false};
       for (int k = 0; k < 3; ++k) {
-        bool use_alt = (m >> k) & 1;
-        if (use_alt && !amb[k]) { ok = false; break; }
-        key.k[k] = use_alt ? alt[k] : base[k];
+        double u = y[k] / quantum;
+        base[k] = (int64_t)std::llround(u);
+        double fr = u - std::floor(u);
+        alt[k] = fr < 0.5 ? base[k] + 1 : base[k] - 1;
+        amb[k] = std::fabs(fr - 0.5) < 1e-3;
       }
-      if (!ok) continue;
-      auto it = map.find(key);
-      if (it != map.end()) found = it->second;
-    }
-    if (found < 0) {
-      Key key{{base[0], base[1], base[2]}};
-      map.emplace(key, G);
-      S->l2g[q] = G++;
-      S->owner[q] = 1;
-    } else {
-      S->l2g[q] = found;
+      int32_t found = -1;
+      for (int m = 0; m < 8 && found < 0; ++m) {
+        Key key;
+        bool ok = true;
+        for (int k = 0; k < 3; ++k) {
+          bool use_alt = (m >> k) & 1;
+          if (use_alt && !amb[k]) { ok = false; break; }
+          key.k[k] = use_alt ? alt[k] : base[k];
+        }
+        if (!ok) continue;
+        auto it = map.find(key);
+        if (it != map.end()) found = it->second;
+      }
+      if (found < 0) {
+        Key key{{base[0], base[1], base[2]}};
+        map.emplace(key, G);
+        S->l2g[q] = G++;
+        S->owner[q] = 1;
+      } else {
+        S->l2g[q] = found;
+      }
     }
   }
   S->G = G;
@@ -480,16 +661,16 @@ int build_setup(const selbm_mesh &mesh, int lattice, int N, Setup *S, std::strin
     }
 
   // wall faces: outward normal +-grad r_l/|grad r_l|, w_s J_s = prod(tangential w) J |grad r_l|
-  S->wall_u.assign((size_t)std::max(mesh.nwalls, 0) * 3, 0.0);
-  for (int k = 0; k < mesh.nwalls; ++k)
-    for (int c = 0; c < dim; ++c) S->wall_u[k * 3 + c] = mesh.wall_velocity ? mesh.wall_velocity[k * dim + c] : 0.0;
+  S->wall_u.assign((size_t)std::max(mi.nwalls, 0) * 3, 0.0);
+  for (int k = 0; k < mi.nwalls; ++k)
+    for (int c = 0; c < dim; ++c) S->wall_u[k * 3 + c] = mi.wall_velocity ? mi.wall_velocity[k * dim + c] : 0.0;
   S->walls.clear();
   S->wall_off.assign(E + 1, 0);
   for (int e = 0; e < E; ++e) {
     for (int f = 0; f < 2 * dim; ++f) {
-      int wid = mesh.face_bc ? mesh.face_bc[(size_t)e * 2 * dim + f] : 0;
+      int wid = mi.face_bc ? mi.face_bc[(size_t)e * 2 * dim + f] : 0;
       if (wid <= 0) continue;
-      if (wid > mesh.nwalls) { *err = "face_bc refers to a wall id beyond nwalls"; return SELBM_ERR_MESH; }
+      if (wid > mi.nwalls) { *err = "face_bc refers to a wall id beyond nwalls"; return SELBM_ERR_MESH; }
       int axis = f / 2, side = f % 2;
       for (int p = 0; p < Np; ++p) {
         if (ijk[3 * p + axis] != (side ? N : 0)) continue;
@@ -525,6 +706,29 @@ int build_setup(const selbm_mesh &mesh, int lattice, int N, Setup *S, std::strin
       }
   S->min_spacing = hmin;
   return SELBM_OK;
+}
+
+int build_setup(const selbm_mesh &mesh, int lattice, int N, Setup *S, std::string *err) {
+  MeshInput mi;
+  mi.dim = mesh.dim;
+  mi.nelem = mesh.nelem;
+  mi.corners = &mesh;
+  mi.face_bc = mesh.face_bc;
+  mi.nwalls = mesh.nwalls;
+  mi.wall_velocity = mesh.wall_velocity;
+  if (!mesh.verts) { *err = "mesh has no elements"; return SELBM_ERR_ARG; }
+  return build_setup_impl(mi, lattice, N, S, err);
+}
+
+int build_setup_nodes(const selbm_mesh_nodes &mesh, int lattice, int N, Setup *S, std::string *err) {
+  MeshInput mi;
+  mi.dim = mesh.dim;
+  mi.nelem = mesh.nelem;
+  mi.nodes = &mesh;
+  mi.face_bc = mesh.face_bc;
+  mi.nwalls = mesh.nwalls;
+  mi.wall_velocity = mesh.wall_velocity;
+  return build_setup_impl(mi, lattice, N, S, err);
 }
 
 }  // namespace slb

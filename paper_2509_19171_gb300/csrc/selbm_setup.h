@@ -12,7 +12,7 @@ namespace slb {
 
 constexpr double kCs2 = 1.0 / 3.0;
 constexpr int kMaxQ = 27;
-constexpr int kMaxN = 12;
+constexpr int kMaxN = 14;
 
 struct Lattice {
   int dim = 0, Q = 0;
@@ -76,5 +76,7 @@ struct Setup {
 
 // Returns SELBM_OK or an error code with a message in *err.
 int build_setup(const selbm_mesh &mesh, int lattice, int N, Setup *S, std::string *err);
+// The same from GLL node coordinates and face connectivity.
+int build_setup_nodes(const selbm_mesh_nodes &mesh, int lattice, int N, Setup *S, std::string *err);
 
 }  // namespace slb

@@ -218,7 +218,7 @@ __device__ __forceinline__ void tile_dense3(Real *sf, int tid, const Real *M, co
 }
 
 template <typename Real, int LAT, int n, bool AFFINE, int MODE>
-__global__ void __launch_bounds__(kProThreads, sizeof(Real) == 4 ? (MODE == PRO_LEARNED ? 3 : 4) : 1)
+__global__ void __launch_bounds__(kProThreads, sizeof(Real) == 4 ? (MODE == PRO_LEARNED ? 3 : 4) : (MODE == PRO_LEARNED ? 1 : 2))
 prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedIn<Real, n> c) {
   constexpr int Q = LT<LAT>::v.Q, DIM = 3, Np = n * n * n, T = kProThreads, NW = T / 32, H = kHidden, nin = 2 * n;
   using TI = Tile<Real, n, DIM>;

@@ -135,6 +135,7 @@ def test_headline_learned_fp32_subset_out_of_range(P):
     # copy it returns without counting): three steps have counted the filters of two
     st = s.learned_status()
     assert st["fixed_element_steps"] == nfix[0] + nfix[1] and st["fallback_flag"] == 0
+    assert s.sync() == 0                                 # per-element fallbacks are routine: plain OK
 
 
 def test_headline_learned_fp32_drift_fallback(P):
@@ -153,6 +154,9 @@ def test_headline_learned_fp32_drift_fallback(P):
     f = o.step_learned(f, params, lo, hi)
     f = o.step(o.step(f))
     s.step(4)
+    assert s.sync() == P.OK_FALLBACK                    # the synchronising calls report it
+    s.diagnostics()
+    assert s.fallback_engaged
     assert rel(s.get_state(), o.to_local(f)) <= TOL32
     assert s.learned_status()["fallback_flag"] == 1
 

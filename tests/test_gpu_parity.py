@@ -161,11 +161,11 @@ def test_single_periodic_element(P):
     check_one_step(P, o, s, f, 1e-12)
 
 
-@pytest.mark.parametrize("N", [2, 12])
+@pytest.mark.parametrize("N", [2, 12, 14])
 def test_extreme_orders(P, N):
     mesh = W.box_mesh((3, 2), (0, 0), (1, 1), (True, False), walls={2: 1, 3: 2},
                       wall_velocity=[[0, 0], [0.01, 0]])
-    filt = {"shape": 0, "gamma": 0.1, "kc": 1.0} if N == 2 else {"shape": 1, "gamma": 0.1, "kc": 10.0}
+    filt = {"shape": 0, "gamma": 0.1, "kc": 1.0} if N == 2 else {"shape": 1, "gamma": 0.1, "kc": float(N - 2)}
     o, s = pair(P, mesh, "D2Q9", N, 1e-2, filt=filt)
     f = random_continuous_state(o, 0.02, 5)
     f = check_one_step(P, o, s, f, 1e-12)

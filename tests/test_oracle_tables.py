@@ -84,7 +84,7 @@ def test_gll_golden_n4():
     assert np.abs(gll.gll_weights(4, xi) - ref[:, 1]).max() < 1e-15
 
 
-@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8, 10, 12])
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8, 10, 12, 14])
 def test_gll_exactness(N):
     """D_hat differentiates x^m exactly for m <= N; GLL quadrature is exact to degree 2N-1 (P2)."""
     xi = gll.gll_nodes(N)

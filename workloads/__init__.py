@@ -1,10 +1,12 @@
 """Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
 
 This module holds *data only*: element corner coordinates, boundary tags,
-periodic lengths, wall velocities and closed-form initial fields.  It contains
-none of the method's arithmetic (no GLL points, no metrics, no lattice
-tables): both the CUDA library and the CPU oracle map the corners to their own
-GLL nodes and evaluate the initial fields there.
+periodic lengths, wall velocities and closed-form initial fields, and the node
+form of a mesh (node coordinates of the element maps at reference points the
+caller supplies, face connectivity found by matching faces).  It contains none
+of the method's arithmetic (no GLL points, no metrics, no lattice tables): both
+the CUDA library and the CPU oracle map the corners (or interpolate the nodes) to
+their own GLL nodes and evaluate the initial fields there.
 
 Mesh conventions (shared interface, documented in include/selbm.h):
 
@@ -169,6 +171,129 @@ def pipe_mesh(n_core=8, n_radial=6, grading=1.3, n_axial=32, length=10.0, radius
 # ----------------------------------------------------------------------------
 # closed-form initial fields (paper's test problems)
 # ----------------------------------------------------------------------------
+
+@dataclass
+class NodeMeshSpec:
+    """Mesh given by the node coordinates of each element's map and its face connectivity
+    (the selbm_mesh_nodes form of include/selbm.h).
+
+    * ``xyz[e, k, p]``: coordinate k of the element's node p = i + n j (+ n^2 l), n = order + 1,
+      at the reference points the caller chose (the order-``order`` GLL points for the library).
+    * ``face_nbr[e, f]``: neighbour element across face f or -1; ``face_nbr_face[e, f]`` its face;
+      ``face_orient[e, f]``: bit 0 swaps the face coordinates (a, b), bit 1 flips a, bit 2 flips b
+      (face coordinates: the two tangential node indices in increasing axis order).
+    * ``bc[e, f]``: 0 interior / periodic / open, k >= 1 wall k with ``wall_velocity[k-1]``.
+    """
+    dim: int
+    order: int
+    xyz: np.ndarray              # [E, dim, (order+1)**dim] float64
+    face_nbr: np.ndarray         # [E, 2*dim] int32
+    face_nbr_face: np.ndarray    # [E, 2*dim] int8
+    face_orient: np.ndarray      # [E, 2*dim] int8
+    bc: np.ndarray               # [E, 2*dim] int32
+    wall_velocity: np.ndarray    # [nwalls, dim] float64
+    name: str = "nodes"
+
+    @property
+    def nelem(self) -> int:
+        return int(self.xyz.shape[0])
+
+
+def _face_local(n, dim, f):
+    """Local node indices of face f in face-coordinate order (a fastest)."""
+    axis, fixed = f // 2, (n - 1) * (f % 2)
+    out = []
+    tang = [k for k in range(dim) if k != axis]
+    rng_b = range(n) if dim == 3 else range(1)
+    for b in rng_b:
+        for a in range(n):
+            idx = [0, 0, 0]
+            idx[axis] = fixed
+            idx[tang[0]] = a
+            if dim == 3:
+                idx[tang[1]] = b
+            out.append(idx[0] + n * idx[1] + n * n * idx[2])
+    return np.array(out)
+
+
+def _orient(code, m, a, b):
+    u, v = (b, a) if code & 1 else (a, b)
+    return (m - u if code & 2 else u), (m - v if code & 4 else v)
+
+
+def node_mesh(mesh, ref_points, deform=None, rotate=(), name="nodes"):
+    """Node form of a straight-sided corner mesh: the (bi/tri)linear map of each element's
+    corners evaluated at the tensor product of ``ref_points`` (reference coordinates in
+    [-1, 1], ascending, symmetric), then ``deform`` (x[n, dim] -> x[n, dim]) applied to every
+    node, and the local frames of the elements in ``rotate`` turned by 90 degrees about t (in 2D
+    about the normal): their new node (i, j, l) is the old node (m - j, i, l), m = len - 1.
+    Connectivity comes from matching faces whose nodes coincide up to one translation (zero
+    inside the domain, a period of ``mesh`` across periodic faces)."""
+    xi = np.asarray(ref_points, float)
+    n, dim, E = len(xi), mesh.dim, mesh.nelem
+    m = n - 1
+    idx = np.indices((n,) * dim).reshape(dim, -1)[::-1]           # row 0 = i (fastest)
+    Np = n ** dim
+    xyz = np.zeros((E, dim, Np))
+    bc = np.array(mesh.bc, np.int32).copy()
+    rot = set(int(e) for e in rotate)
+    for e in range(E):
+        C = mesh.verts[e]
+        ii = idx.copy()
+        if e in rot:
+            ii = np.stack([m - idx[1], idx[0]] + ([idx[2]] if dim == 3 else []))
+        lam = [np.stack([(1 - xi[ii[k]]) / 2, (1 + xi[ii[k]]) / 2]) for k in range(dim)]
+        x = np.zeros((Np, dim))
+        for c in range(2 ** dim):
+            bits = [(c >> k) & 1 for k in range(dim)]
+            wgt = np.prod([lam[k][bits[k]] for k in range(dim)], axis=0)
+            x += wgt[:, None] * C[c][None, :]
+        if deform is not None:
+            x = deform(x)
+        xyz[e] = x.T
+        if e in rot:
+            perm = [2, 3, 1, 0] + ([4, 5] if dim == 3 else [])
+            bc[e] = np.array(mesh.bc[e])[perm]
+    nf = 2 * dim
+    period = np.asarray(mesh.period, float)
+    faces = {}
+    for e in range(E):
+        for f in range(nf):
+            faces[(e, f)] = xyz[e][:, _face_local(n, dim, f)].T         # [nface, dim]
+    scale = float(np.ptp(xyz.transpose(0, 2, 1).reshape(-1, dim), axis=0).max())
+    tol = 1e-9 * scale
+
+    def wrapped_key(P):
+        c = P.mean(0).copy()
+        for k in range(dim):
+            if period[k] > 0:
+                c[k] = np.mod(c[k] - mesh.origin[k] + 0.5 * tol, period[k])
+        return tuple(np.round(c / (1e-6 * scale)).astype(np.int64))
+    buckets = {}
+    for key, P in faces.items():
+        buckets.setdefault(wrapped_key(P), []).append(key)
+    face_nbr = np.full((E, nf), -1, np.int32)
+    face_nbr_face = np.zeros((E, nf), np.int8)
+    face_orient = np.zeros((E, nf), np.int8)
+    nb = n if dim == 3 else 1
+    for keys in buckets.values():
+        for (e, f) in keys:
+            for (e2, f2) in keys:
+                if (e2, f2) == (e, f):
+                    continue
+                A, B = faces[(e, f)], faces[(e2, f2)]
+                for code in (range(8) if dim == 3 else (0, 2)):
+                    mp = [_orient(code, m, a, b) for b in range(nb) for a in range(n)]
+                    d = np.array([B[a2 + n * b2] for a2, b2 in mp]) - A
+                    if np.abs(d - d[0]).max() > tol:
+                        continue
+                    ok = all(abs(d[0][k]) <= tol or (period[k] > 0 and abs(abs(d[0][k]) - period[k]) <= tol)
+                             for k in range(dim))
+                    if ok and face_nbr[e, f] < 0:
+                        face_nbr[e, f], face_nbr_face[e, f], face_orient[e, f] = e2, f2, code
+    return NodeMeshSpec(dim, m, xyz, face_nbr, face_nbr_face, face_orient, bc,
+                        np.asarray(mesh.wall_velocity, float).reshape(-1, dim), name)
+
 
 def couette_init(rho0=1.0):
     def f(x):
