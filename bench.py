@@ -42,7 +42,27 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
+
+
+def fp64_peak(torch, n=4096, reps=3):
+    """Measured FP64 arithmetic peak of this GPU: best of `reps` cuBLAS DGEMMs of n^3 (2 n^3
+    flops each), CUDA events on the current stream.  On GB300 the FP64 tensor rate equals the
+    FP64 FMA rate, so this is the ceiling of the FP64 form's DFMA-bound kernels."""
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.mm(a, b)
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        torch.mm(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
 def measured_traffic(kernel_key, units):
@@ -270,26 +290,67 @@ def e2e_run(P, torch, case, form, steps):
     return ms, h2d, d2h
 
 
-def cpu_baseline(case, seconds=12.0):
-    """The oracle, as it stands, on a bounded sample of the workload: same
-    lattice, order and filter on 4^3 elements of the same periodic cube."""
+def _oracle_sample(case, n=4):
     from oracle.selbm import OracleSELBM
     L = 2 * math.pi
-    n = 4
     mesh = W.box_mesh((n, n, n), (0, 0, 0), (L, L, L), (True, True, True))
-    o = OracleSELBM(mesh, case.lattice, case.order, case.nu, cfl=case.cfl, filt=case.filt)
-    f = o.initial_state_from(case.init)
-    f = o.step(f)
+    return OracleSELBM(mesh, case.lattice, case.order, case.nu, cfl=case.cfl, filt=case.filt)
+
+
+def _oracle_rate(args):
+    """Updates/s of the oracle stepping the sample for about `seconds` (one process, 1 thread)."""
+    case_name, n_el, seconds = args
+    case = workload(case_name)
+    o = _oracle_sample(case, n_el)
+    f = o.step(o.initial_state_from(case.init))
     t0 = time.perf_counter()
     k = 0
     while time.perf_counter() - t0 < seconds:
         f = o.step(f)
         k += 1
     dt = time.perf_counter() - t0
-    upd = o.E * o.Np * o.Q * k
-    return {"value": upd / dt, "unit": "node-pop updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{case.lattice} N={case.order} TGV on {n}^3 elements ({o.E * o.Np * o.Q} updates/step), "
-                      f"{k} steps in {dt:.1f} s, numpy float64, 1 thread"}
+    return o.E * o.Np * o.Q * k / dt, k, dt, o.E * o.Np * o.Q
+
+
+def cpu_model():
+    """CPU model of this host (lscpu's model name, else /proc/cpuinfo, else platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(case, seconds=12.0, all_cores=True):
+    """The oracle, as it stands, on a bounded sample of the workload: same lattice, order and
+    filter on 4^3 elements of the same periodic cube; one thread, and every host core running
+    its own copy of the sample (spawned processes, one BLAS thread each)."""
+    rate1, k, dt, upd = _oracle_rate((case.name, 4, seconds))
+    ncpu = os.cpu_count() or 1
+    out = {"value": rate1, "unit": "node-pop updates/s", "cores": 1, "kind": "oracle",
+           "cpu_model": cpu_model(), "nproc": ncpu,
+           "sample": f"{case.lattice} N={case.order} TGV on 4^3 elements ({upd} updates/step), "
+                     f"{k} steps in {dt:.1f} s, numpy float64, 1 thread"}
+    if all_cores and ncpu > 1:
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(ncpu) as pool:
+            res = pool.map(_oracle_rate, [(case.name, 4, seconds)] * ncpu)
+        total = sum(r[0] for r in res)
+        out.update({"value": total, "cores": ncpu, "value_1thread": rate1,
+                    "sample": out["sample"] + f"; all cores: {ncpu} processes x the same sample for "
+                              f"{seconds:.0f} s each, summed"})
+    return out
 
 
 def workload_config(case, form, world):
@@ -325,9 +386,9 @@ def main():
         cb = None
         vals = []
         for _ in range(args.warmup):
-            cpu_baseline(case, seconds=2.0)
+            cpu_baseline(case, seconds=2.0, all_cores=False)
         for _ in range(args.steps):
-            cb = cpu_baseline(case, seconds=3.0)
+            cb = cpu_baseline(case, seconds=3.0, all_cores=False)
             vals.append(cb["value"])
         v = statistics.median(vals)
         cb["value"] = v
@@ -367,6 +428,7 @@ def main():
     main_form = "fp32dev_learned" if "fp32dev_learned" in forms else forms[-1]
     order = [f for f in forms if f != main_form] + [main_form]
     results, fields, clocks = {}, {}, None
+    fp64_tflops = None
     ksteps = min(args.steps, 5)
     for form in order:
         rsz = 8 if form == "fp64" else 4
@@ -404,10 +466,13 @@ def main():
             "stage23_bytes": kb["stage23"], "stage23_ms": per.get("stage23"),
         }
         if form == "fp64":
+            if fp64_tflops is None:
+                fp64_tflops = fp64_peak(torch)
             st_ms = (t["stage1"][0] + t["stage23"][0]) / max(t["stage1"][1] + t["stage23"][1], 1)
             entry["stage_flops"] = (f1 + 2 * f23) / 3
             entry["stage_ms"] = st_ms
-            entry["stage_fp64_frac"] = entry["stage_flops"] / (st_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
+            entry["fp64_peak_tflops"] = fp64_tflops
+            entry["stage_fp64_frac"] = entry["stage_flops"] / (st_ms * 1e-3) / 1e12 / fp64_tflops
         if learned:
             st = s.learned_status()
             entry["learned"] = {"fallback_flag": st["fallback_flag"],
@@ -435,10 +500,9 @@ def main():
     r = results[main_form]
     if main_form == "fp64":
         achieved = r["stage_flops"] / (r["stage_ms"] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "stage_fast_kernel (FP64 pipe)", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe: 2.07/clk/SM)",
-                "traffic": None}
+        roof = {"bound": "alu", "kernel": "stage kernels (FP64 pipe)", "achieved": achieved,
+                "peak": fp64_tflops, "unit": "TFLOP/s", "frac": achieved / fp64_tflops,
+                "peak_source": "measured on this GPU: best cuBLAS DGEMM 4096^3", "traffic": None}
     else:
         # dominant kernel: the stage 2/3 kernel (two launches per step)
         geom = "affine" if info["affine"] else "curved"

@@ -4,17 +4,17 @@ Every number here is computed by the CUDA library (features, per-element errors
 against the order N+4 run, network training and inference); this module only
 schedules the runs and moves tensors.
 
-Data: runs of the same case at the fixed filter strengths of a sweep
-(default gamma in {0.01, 0.03, 0.1, 0.3} at kc = N-2, optionally kc in
-{N-3, N-2, N-1}) and one run at order N+4 with a time step dividing the
-order-N step.  At each snapshot every element gets the features of the
+Data: runs of the same case at the fixed filter settings of a sweep
+(gamma in {0.01, 0.03, 0.1, 0.3} x kc in {N-3, N-2, N-1}) and one run at order
+N+4 with a time step dividing the order-N step.  At each snapshot every element gets the features of the
 default-filter run (the one the control replaces) and the label (gamma*, kc*)
 of the sweep setting whose element error against the N+4 run is smallest;
 when the default setting's error is within `tie_margin` of the smallest, the
 label is the default (in well-resolved regions the settings differ by less
 than the noise of the reference and the control should keep the fixed filter).
 
-python -m paper_2509_19171_gb300.learn --case tgv3d --out weights/...npz
+python -m paper_2509_19171_gb300.learn --summary learn.json   (Taylor-Green 16^3 + double shear
+layer 32^2 at N = 7, about 1.2M element snapshots; weights to weights/learned_filter_tgv3d_shear_n7.npz)
 """
 from __future__ import annotations
 
@@ -80,6 +80,8 @@ def generate(mesh, lattice, N, nu, inits, snapshots, interval, start=0, gammas=D
             ref.step(interval * ref_sub)
             feat = runs[base_i].features()
             errs = torch.stack([h.element_errors(ref) for h in runs])         # [runs, E]
+            # a sweep setting that has gone unstable (non-finite errors) is never the best one
+            errs = torch.nan_to_num(errs, nan=float("inf"), posinf=float("inf"))
             best = torch.argmin(errs, dim=0)
             if tie_margin > 0:
                 emin = errs.min(dim=0).values
@@ -118,8 +120,10 @@ def train(X, Y, N, epochs=30, batch=1024, lr=2e-3, seed=0, verbose=False):
 
 
 def evaluate(mesh, lattice, N, nu, init, steps, params, lo, hi, default_gamma=0.1, precision=FP32DEV, cfl=0.5,
-             checkpoints=4):
-    """Total error against the N+4 run for the fixed default filter and for the learned control."""
+             checkpoints=4, constants=()):
+    """Total error against the N+4 run for the fixed default filter, for the learned control and
+    (same reference run) for fixed filters at the (gamma, kc) settings in `constants`; an
+    unstable setting reports inf."""
     default = {"shape": 0, "gamma": default_gamma, "kc": float(N - 2)}
     fixed = SELBM(mesh, lattice, N, nu, cfl=cfl, precision=precision, filt=default)
     learned = SELBM(mesh, lattice, N, nu, dt=fixed.dt, precision=precision, filt=default)
@@ -128,22 +132,30 @@ def evaluate(mesh, lattice, N, nu, init, steps, params, lo, hi, default_gamma=0.
     probe_r.close()
     ref = SELBM(mesh, lattice, N + 4, nu, dt=fixed.dt / ref_sub, precision=FP32DEV,
                 filt={"shape": 0, "gamma": default_gamma, "kc": float(N + 2)})
-    for h in (fixed, learned, ref):
+    consts = [SELBM(mesh, lattice, N, nu, dt=fixed.dt, precision=precision, filt={"shape": 0, "gamma": g, "kc": k})
+              for g, k in constants]
+    for h in [fixed, learned, ref] + consts:
         h.init_from(init)
     learned.set_learned_filter(params, lo, hi)
     out = []
     per = max(steps // checkpoints, 1)
     fallback = 0
+
+    def total(h):
+        v = float(h.element_errors(ref).sum().item())
+        return v if math.isfinite(v) else float("inf")
     for c in range(checkpoints):
-        for h in (fixed, learned):
+        for h in [fixed, learned] + consts:
             h.step(per)
         ref.step(per * ref_sub)
-        ef = float(fixed.element_errors(ref).sum().item())
-        el = float(learned.element_errors(ref).sum().item())
         st = learned.learned_status()
         fallback += st["fixed_element_steps"]
-        out.append({"step": (c + 1) * per, "err_fixed": ef, "err_learned": el, "fallback_flag": st["fallback_flag"]})
-    for h in (fixed, learned, ref):
+        row = {"step": (c + 1) * per, "err_fixed": total(fixed), "err_learned": total(learned),
+               "fallback_flag": st["fallback_flag"]}
+        if consts:
+            row["err_constants"] = [total(h) for h in consts]
+        out.append(row)
+    for h in [fixed, learned, ref] + consts:
         h.close()
     return out, fallback
 
@@ -160,67 +172,82 @@ def tgv_inits(count, seed0=1, U0=0.05):
     return out
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="tgv3d", choices=["tgv3d"])
-    ap.add_argument("--n", type=int, default=8, help="elements per side of the training cube")
-    ap.add_argument("--seeds", type=int, default=3)
-    ap.add_argument("--snapshots", type=int, default=24)
-    ap.add_argument("--interval", type=int, default=100)
-    ap.add_argument("--start", type=int, default=400)
-    ap.add_argument("--epochs", type=int, default=40)
-    ap.add_argument("--all-kc", action="store_true", help="sweep kc in {N-3, N-2, N-1} as well as gamma")
-    ap.add_argument("--eval-steps", type=int, default=0, help="held-out evaluation length (0: data horizon)")
-    ap.add_argument("--tie-margin", type=float, default=0.0)
-    ap.add_argument("--extra-n", type=int, default=0, help="also take data from a cube of this size")
-    ap.add_argument("--extra-start", type=int, default=1600)
-    ap.add_argument("--extra-interval", type=int, default=200)
-    ap.add_argument("--extra-seeds", type=int, default=3)
-    ap.add_argument("--out", default=os.path.join(WEIGHTS_DIR, "learned_filter_tgv3d_n7_d3q27.npz"))
-    ap.add_argument("--check-n", type=int, default=16, help="cube size at which to report the fallback rate")
-    ap.add_argument("--check-steps", type=int, default=400)
-    args = ap.parse_args()
+def shear_inits(count, seed0=3, U0=0.04):
+    """Double-shear-layer initial fields shifted along x by seeded fractions of the period."""
     import workloads as W
-    case = W.tgv3d_case(n=args.n)
-    N = case.order
+    rng = np.random.default_rng(seed0)
+    out = []
+    for _ in range(count):
+        sh = rng.uniform(0, 1)
+        base = W.shear_layer_init(U0=U0)
+        out.append(lambda x, sh=sh, base=base: base(x + np.array([sh, 0.0])))
+    return out
+
+
+def main():
+    """Data from Taylor-Green (16^3 hexes, N = 7, D3Q27) and the double shear layer (32^2
+    quads at N = 7, D2Q9: the same 2(N+1) = 16 features), labels from the gamma x kc sweep
+    against the order N+4 run, training, then a held-out Taylor-Green phase: total error
+    against the N+4 run of the learned control, of the paper's fixed filter it replaces, and
+    of the best single fixed setting of the sweep."""
+    import json
+    import torch
+    import workloads as W
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--tgv-n", type=int, default=16, help="elements per side of the Taylor-Green cube")
+    ap.add_argument("--tgv-seeds", type=int, default=1)
+    ap.add_argument("--tgv-steps", type=int, default=9500, help="run length (t = 6 L0/U0 at 9,500 steps)")
+    ap.add_argument("--tgv-start", type=int, default=400)
+    ap.add_argument("--tgv-interval", type=int, default=50)
+    ap.add_argument("--shear-n", type=int, default=32)
+    ap.add_argument("--shear-seeds", type=int, default=2)
+    ap.add_argument("--shear-steps", type=int, default=20000)
+    ap.add_argument("--shear-start", type=int, default=2000)
+    ap.add_argument("--shear-interval", type=int, default=200)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--eval-steps", type=int, default=9500, help="held-out Taylor-Green length (t = 6 L0/U0)")
+    ap.add_argument("--tie-margin", type=float, default=0.02,
+                    help="keep the default label unless another setting's error is this much smaller")
+    ap.add_argument("--out", default=os.path.join(WEIGHTS_DIR, "learned_filter_tgv3d_shear_n7.npz"))
+    ap.add_argument("--summary", default=None, help="JSON summary of the run")
+    args = ap.parse_args()
+    N = 7
+    kcs = (float(N - 3), float(N - 2), float(N - 1))
     t0 = time.time()
-    kcs = (float(N - 3), float(N - 2), float(N - 1)) if args.all_kc else None
-    X, Y = generate(case.mesh, case.lattice, N, case.nu, tgv_inits(args.seeds), args.snapshots, args.interval,
-                    start=args.start, kcs=kcs, tie_margin=args.tie_margin, verbose=True)
-    extra_eval = None
-    if args.extra_n:
-        import torch
-        ec = W.tgv3d_case(n=args.extra_n)
-        X2, Y2 = generate(ec.mesh, ec.lattice, N, ec.nu, tgv_inits(args.extra_seeds, seed0=7), args.snapshots,
-                          args.extra_interval, start=args.extra_start, kcs=kcs, tie_margin=args.tie_margin, verbose=True)
-        X, Y = torch.cat([X, X2]), torch.cat([Y, Y2])
-        extra_eval = ec
+    tgv = W.tgv3d_case(n=args.tgv_n)
+    snaps = (args.tgv_steps - args.tgv_start) // args.tgv_interval
+    X1, Y1 = generate(tgv.mesh, tgv.lattice, N, tgv.nu, tgv_inits(args.tgv_seeds), snaps, args.tgv_interval,
+                      start=args.tgv_start, kcs=kcs, tie_margin=args.tie_margin, verbose=True)
     t1 = time.time()
-    params, lo, hi, hist = train(X, Y, N, epochs=args.epochs, verbose=True)
+    sh = W.shear_layer_case(n=args.shear_n, order=N)
+    snaps = (args.shear_steps - args.shear_start) // args.shear_interval
+    X2, Y2 = generate(sh.mesh, sh.lattice, N, sh.nu, shear_inits(args.shear_seeds), snaps, args.shear_interval,
+                      start=args.shear_start, kcs=kcs, tie_margin=args.tie_margin, verbose=True)
     t2 = time.time()
-    res, fb = evaluate(case.mesh, case.lattice, N, case.nu, tgv_inits(1, seed0=99)[0],
-                       args.eval_steps or (args.start + args.snapshots * args.interval), params, lo, hi)
-    res_extra = None
-    if extra_eval is not None:
-        res_extra = evaluate(extra_eval.mesh, extra_eval.lattice, N, extra_eval.nu, tgv_inits(1, seed0=99)[0],
-                             args.extra_start + args.snapshots * args.extra_interval, params, lo, hi)
+    X, Y = torch.cat([X1, X2]), torch.cat([Y1, Y2])
+    params, lo, hi, hist = train(X, Y, N, epochs=args.epochs, verbose=True)
+    t3 = time.time()
+    labels, counts = np.unique(Y.cpu().numpy().round(3), axis=0, return_counts=True)
+    sweep = [(g, k) for g in DEFAULT_GAMMAS for k in kcs]
+    held = tgv_inits(1, seed0=99)[0]
+    res, fb = evaluate(tgv.mesh, tgv.lattice, N, tgv.nu, held, args.eval_steps, params, lo, hi, constants=sweep)
+    t4 = time.time()
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
-    np.savez(args.out, params=params, lo=lo, hi=hi, N=N, lattice=case.lattice, samples=int(X.shape[0]),
+    np.savez(args.out, params=params, lo=lo, hi=hi, N=N, lattice=tgv.lattice, samples=int(X.shape[0]),
              loss=np.array(hist, np.float32))
-    big = W.tgv3d_case(n=args.check_n)
-    h = SELBM(big.mesh, big.lattice, N, big.nu, cfl=big.cfl, precision=FP32DEV, filt=big.filt)
-    h.init_from(big.init)
-    h.set_learned_filter(params, lo, hi)
-    h.step(args.check_steps)
-    st = h.learned_status()
-    h.close()
-    print({"samples": int(X.shape[0]), "data_s": round(t1 - t0, 1), "train_s": round(t2 - t1, 1),
-           "label_hist": {f"{g:.2f}/{k:.0f}": int(c) for (g, k), c in
-                          zip(*np.unique(Y.cpu().numpy().round(3), axis=0, return_counts=True))},
-           "eval": res, "fallback_element_steps": fb, "eval_extra": res_extra,
-           "check": {"n": args.check_n, "steps": args.check_steps,
-                     "fallback_fraction": st["fixed_element_steps"] / (big.mesh.nelem * (args.check_steps - 1)),
-                     "flag": st["fallback_flag"]}})
+    summary = {"samples": int(X.shape[0]), "samples_tgv": int(X1.shape[0]), "samples_shear": int(X2.shape[0]),
+               "label_hist": {f"{g:.2f}/{k:.0f}": int(c) for (g, k), c in zip(labels, counts)},
+               "loss_first_last": [float(hist[0]), float(hist[-1])],
+               "eval_tgv_heldout": res, "fallback_element_steps": int(fb),
+               "eval_constants": [{"gamma": g, "kc": k} for g, k in sweep],
+               "seconds": {"data_tgv": round(t1 - t0, 1), "data_shear": round(t2 - t1, 1), "train": round(t3 - t2, 1),
+                           "eval": round(t4 - t3, 1)},
+               "command": "python -m paper_2509_19171_gb300.learn " + " ".join(
+                   f"--{k.replace('_', '-')} {v}" for k, v in vars(args).items() if v is not None and k not in ("out", "summary"))}
+    if args.summary:
+        with open(args.summary, "w") as fh:
+            json.dump(summary, fh, indent=1)
+    print(json.dumps(summary))
 
 
 if __name__ == "__main__":

@@ -9,6 +9,12 @@ the learned control also against the fixed filter it replaces; the butterfly pip
 (8192 hexes, N=7, D3Q19, curved walls, body force) for 1000 steps, the double
 shear layer (32^2, N=8, D2Q9) for 2000 steps.
 
+Sensitivity control ("fp64_perturbed"): the FP64 form started from the same field with
+every deviation f - t rho0 multiplied by 1 + 2^-24 xi (xi = +-1, seeded), i.e. a
+perturbation of the size of one FP32 storage rounding of the state.  Its distance from the
+unperturbed FP64 run is what any FP32-level difference grows to by the flow itself; an
+FP32 form at that distance is at the floor the flow sets, not limited by its arithmetic.
+
 python -m paper_2509_19171_gb300.validate --out validation.json
 """
 from __future__ import annotations
@@ -33,11 +39,23 @@ def _errors(a, b, U0):
             "rho_rms": float(np.sqrt(((ra - rb) ** 2).mean())), "rho_max": float(np.abs(ra - rb).max())}
 
 
+def perturb_fp32_level(h, rho0=1.0, seed=5):
+    """Multiply every deviation f - t rho0 of the handle's state by 1 + 2^-24 xi, xi = +-1."""
+    f = h.get_state()
+    _, t, _ = h.lattice_table()
+    rng = np.random.default_rng(seed)
+    dev = f - t[:, None, None] * rho0
+    xi = rng.integers(0, 2, size=f.shape) * 2.0 - 1.0
+    h.set_state(np.ascontiguousarray(t[:, None, None] * rho0 + dev * (1.0 + 2.0 ** -24 * xi)))
+
+
 def run_case(case, forms, steps, checkpoints, history_every, learned=None):
     handles = {}
     for f in forms:
-        h = from_case(case, precision=FP64 if f == "fp64" else FP32DEV)
+        h = from_case(case, precision=FP64 if f.startswith("fp64") else FP32DEV)
         h.init_from(case.init)
+        if f == "fp64_perturbed":
+            perturb_fp32_level(h, case.rho0)
         if f == "fp32dev_learned":
             w = np.load(learned)
             h.set_learned_filter(w["params"], w["lo"], w["hi"], mass_bound=1e-6)
@@ -98,13 +116,14 @@ def main():
     weights = args.weights
     tgv = W.tgv3d_case()
     tgv_steps = 200 if args.quick else 8000     # t = 5 L0/U0 at dt = 0.0126
-    forms = ["fp64", "fp32dev"] + (["fp32dev_learned"] if os.path.exists(weights) else [])
+    forms = ["fp64", "fp64_perturbed", "fp32dev"] + (["fp32dev_learned"] if os.path.exists(weights) else [])
     if "tgv" in cases:
         res.append(run_case(tgv, forms, tgv_steps, [tgv_steps * 2 // 5, tgv_steps], max(tgv_steps // 40, 1), weights))
     if "pipe" in cases:
         pipe = W.pipe_case()
         pipe_steps = 100 if args.quick else 1000
-        res.append(run_case(pipe, ["fp64", "fp32dev"], pipe_steps, [pipe_steps], max(pipe_steps // 10, 1)))
+        pforms = ["fp64", "fp64_perturbed", "fp32dev"] + (["fp32dev_learned"] if os.path.exists(weights) else [])
+        res.append(run_case(pipe, pforms, pipe_steps, [pipe_steps], max(pipe_steps // 10, 1), weights))
     if "shear" in cases:
         shear = W.shear_layer_case()
         sh_steps = 200 if args.quick else 2000
