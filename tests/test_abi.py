@@ -80,7 +80,7 @@ def test_rejects_bad_meshes(P):
         P.mesh_check(mesh, "D3Q19", 4)                          # lattice/mesh dimension mismatch
     assert ei.value.code == -1
     with pytest.raises(P.SelbmError) as ei:
-        P.mesh_check(mesh, "D2Q9", 13)                          # order out of range
+        P.mesh_check(mesh, "D2Q9", 15)                          # order out of range (2 <= N <= 14)
     assert ei.value.code == -1
     walls = W.box_mesh((2, 2), (0, 0), (1, 1), (True, False), walls={2: 3})
     walls.wall_velocity = np.zeros((1, 2))                      # wall id 3 > nwalls
