@@ -360,8 +360,8 @@ int selbm_mesh_check_nodes(const selbm_mesh_nodes *mesh, int32_t lattice, int32_
  *          the filtered copies of shared nodes)
  *   k = 4: population-split form: prologue (fixed filter + collision, or the
  *          collision alone when no filter is pending)
- * The population-split form is the default for FP32 hexahedral meshes at the
- * compiled orders (D3Q19: N = 4, 7; D3Q27: N = 5, 7).
+ * The population-split form is the default for hexahedral meshes at the
+ * compiled orders (D3Q19: N = 4, 7; D3Q27: N = 5, 7), in both precisions.
  */
 #define SELBM_TIMER_KINDS 5
 int selbm_timers(selbm_t *h, int enable);

@@ -45,8 +45,8 @@ struct selbm {
   int64_t steps = 0;
   bool initialized = false, filter_pending = false, filter_on = false, has_force = false;
   bool use_fast = true;   // SELBM_GENERIC_KERNEL=1 in the environment selects the generic stage kernel
-  // population-split step (prologue + split stages); default for FP32 hexahedral meshes,
-  // SELBM_SPLIT=1 / 0 in the environment forces it on / off where it is compiled
+  // population-split step (prologue + split stages); default for hexahedral meshes at the
+  // compiled orders, SELBM_SPLIT=1 / 0 in the environment forces it on / off where compiled
   bool use_split = false;
   std::vector<double> Vm_h, Vinv_h;   // modal <-> nodal matrices
   // learned per-element filter control
@@ -574,7 +574,7 @@ static int create_impl(SetupFn setup, const selbm_params *params, void *cuda_str
   {
     const char *sp = std::getenv("SELBM_SPLIT");
     const bool ok = h->use_fast && S.dim == 3 && split_compiled(h->lat, S.N);
-    h->use_split = ok && (sp && sp[0] ? sp[0] == '1' : h->prec == SELBM_FP32DEV);
+    h->use_split = ok && (sp && sp[0] ? sp[0] == '1' : true);
   }
   const size_t smem = stage_smem_bytes(h->lat, S.Np, S.n1, h->rsz);
   if (smem > 227 * 1024) { g_create_error = "element tile does not fit in shared memory (use FP32 or a lower order)"; delete h; return SELBM_ERR_ARG; }

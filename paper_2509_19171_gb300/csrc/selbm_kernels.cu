@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) dss_kernel(con
   const Real *__restrict__ f0 = p.f0;
   Real *__restrict__ fout = p.fout;
   const size_t G = p.Gs;                 // population stride
+  const bool use_f0 = p.A != Real(0);
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < p.Gb; u += gridDim.x * blockDim.x) {
     const int c0 = p.bnode_off[u], c1 = p.bnode_off[u + 1];
     const size_t gid = p.bnode_g[u];
@@ -320,7 +321,8 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) dss_kernel(con
           for (int k = 0; k < DIM; ++k) eg += (Real)c_e[LAT][a][k] * ga[k];
           Fs = wt<Real>(LAT, a) * eg * rho * Real(3);
         }
-        fout[(size_t)a * G + gid] = p.A * f0[(size_t)a * G + gid] + p.B * fin[(size_t)a * G + gid] + s[al] * minv + Bdt * Fs;
+        const Real base = use_f0 ? p.A * f0[(size_t)a * G + gid] : Real(0);   // stage 1: A = 0
+        fout[(size_t)a * G + gid] = base + p.B * fin[(size_t)a * G + gid] + s[al] * minv + Bdt * Fs;
       }
     }
   }

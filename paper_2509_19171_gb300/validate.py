@@ -29,7 +29,7 @@ import numpy as np
 from . import FP32DEV, FP64, from_case
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-WEIGHTS = os.path.join(HERE, "weights", "learned_filter_tgv3d_n7_d3q27.npz")
+WEIGHTS = os.path.join(HERE, "weights", "learned_filter_tgv3d_shear_n7.npz")
 
 
 def _errors(a, b, U0):

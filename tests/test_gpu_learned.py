@@ -203,7 +203,10 @@ def test_learned_drift_fallback(P):
 def test_learned_ab_gain(P):
     """Train on small double-shear-layer runs (sweep gamma in {0.01, 0.03, 0.1, 0.3}, labels
     from the order N+4 run), then compare the total error against the N+4 run on a held-out
-    shift: learned control vs the fixed filter it replaces."""
+    shift: learned control vs the fixed filter it replaces.  The control must gain: its error is
+    below the fixed filter's at every checkpoint and lower by at least 5 % on average over the
+    checkpoints (measured on a GB300: 13.0, 15.7, 13.4 and 1.8 %, mean 11.0 %; training and
+    evaluation are deterministic)."""
     from paper_2509_19171_gb300 import learn
     N = 6
     mesh = W.box_mesh((6, 6), (0, 0), (1, 1), (True, True))
@@ -221,5 +224,7 @@ def test_learned_ab_gain(P):
     gain = 1.0 - res[-1]["err_learned"] / res[-1]["err_fixed"]
     print("A/B (learned vs fixed) relative error gain per checkpoint:",
           [round(1.0 - r["err_learned"] / r["err_fixed"], 4) for r in res], "fallback element-steps:", fb)
-    assert res[-1]["err_learned"] <= 1.05 * res[-1]["err_fixed"], res
+    gains = [1.0 - r["err_learned"] / r["err_fixed"] for r in res]
     assert np.isfinite(gain)
+    assert min(gains) > 0.0, gains
+    assert float(np.mean(gains)) >= 0.05, gains
