@@ -56,6 +56,8 @@ struct selbm {
   void *d_Vm = nullptr, *d_Vinv = nullptr, *d_sigma_e = nullptr, *d_lo = nullptr, *d_hi = nullptr, *d_fixsig = nullptr;
   __nv_bfloat16 *d_W = nullptr;
   double *d_acc = nullptr;
+  void *d_nq = nullptr;          // [2][Gs] rho - rho0 and |u| on unique nodes (learned control, split form)
+  void *d_X = nullptr;           // [E][2n] element features (learned control, split form)
   int *d_flag = nullptr, *d_nfb = nullptr;
   int wall_max = 0;
   int n_wallpts = 0;             // wall points (element, node) over all elements
@@ -180,6 +182,8 @@ cudaError_t upload_real(selbm *h) {
   if ((e = alloc(&h->d_lo, 2 * S.n1 * sizeof(Real)))) return e;
   if ((e = alloc(&h->d_hi, 2 * S.n1 * sizeof(Real)))) return e;
   if ((e = alloc((void **)&h->d_acc, 8 * sizeof(double)))) return e;
+  if ((e = alloc(&h->d_nq, 2 * (size_t)h->Gs() * sizeof(Real)))) return e;
+  if ((e = alloc(&h->d_X, 2 * (size_t)S.n1 * S.E * sizeof(Real)))) return e;
   if ((e = alloc((void **)&h->d_flag, 2 * sizeof(int)))) return e;
   if ((e = alloc((void **)&h->d_nfb, 2 * sizeof(int)))) return e;
   if ((e = alloc((void **)&h->d_W, (size_t)mlp_nparams(2 * S.n1) * sizeof(__nv_bfloat16)))) return e;
@@ -311,6 +315,12 @@ cudaError_t launch_split_prologue(selbm *h, int mode, const KParams<Real> &p, co
   return err;
 }
 
+// the learned step prologue of the split form: the control (node features + network per
+// element -> sigma_e), the filter with each element's sigma_e + collision of interior nodes +
+// weighted shares of boundary nodes, the drift check, the assembly + collision of shared nodes
+template <typename Real>
+cudaError_t launch_split_learned(selbm *h, const KParams<Real> &p);
+
 template <typename Real>
 cudaError_t launch_split_collide(selbm *h, int which, const KParams<Real> &p) {
   if (h->lat == SELBM_D3Q19) return split_collide_d3q19<Real>(which, p, h->stream);
@@ -328,6 +338,19 @@ LearnedPtrs<Real> learned_ptrs(selbm *h, bool with_drift) {
   return lp;
 }
 
+template <typename Real>
+cudaError_t launch_split_learned(selbm *h, const KParams<Real> &p) {
+  const SplitHost sh = split_host(h);
+  const LearnedPtrs<Real> lp = learned_ptrs<Real>(h, true);
+  cudaError_t e = cudaErrorInvalidValue;
+  if (h->lat == SELBM_D3Q19) split_control_d3q19<Real>(h->S.N, p, sh, lp, (Real *)h->d_nq, (Real *)h->d_X, h->d_mass, h->stream, &e);
+  else if (h->lat == SELBM_D3Q27) split_control_d3q27<Real>(h->S.N, p, sh, lp, (Real *)h->d_nq, (Real *)h->d_X, h->d_mass, h->stream, &e);
+  if (e) return e;
+  if ((e = launch_split_prologue<Real>(h, PRO_LEARNED, p, lp))) return e;
+  if ((e = launch_drift_check(h->d_acc, h->d_flag, h->mass_bound, h->ke_bound, h->has_force ? 0 : 1, h->stream))) return e;
+  return launch_split_collide<Real>(h, 1, p);
+}
+
 // one time step of the population-split form: prologue (pending filter + collision,
 // f^0 on unique nodes), then three advection stages, each = split kernel + assembly
 template <typename Real>
@@ -339,9 +362,7 @@ cudaError_t enqueue_step_split(selbm *h, bool apply_filter) {
   p.stage = 1; p.A = Real(0); p.B = Real(1);
   if (apply_filter && h->learned) {
     cudaEvent_t t0 = h->mark_begin();
-    if ((e = launch_split_prologue<Real>(h, PRO_LEARNED, p, learned_ptrs<Real>(h, true)))) return e;
-    if ((e = launch_drift_check(h->d_acc, h->d_flag, h->mass_bound, h->ke_bound, h->has_force ? 0 : 1, h->stream))) return e;
-    if ((e = launch_split_collide<Real>(h, 1, p))) return e;
+    if ((e = launch_split_learned<Real>(h, p))) return e;
     h->mark_end(3, t0);
   } else {
     cudaEvent_t t0 = h->mark_begin();
@@ -391,9 +412,7 @@ cudaError_t enqueue_step_printed(selbm *h, bool apply_filter) {
     p.stage = 1; p.A = Real(0); p.B = Real(1);
     p.fin = FA; p.f0out = F0;
     if (apply_filter && h->learned) {
-      if ((e = launch_split_prologue<Real>(h, PRO_LEARNED, p, learned_ptrs<Real>(h, true)))) return e;
-      if ((e = launch_drift_check(h->d_acc, h->d_flag, h->mass_bound, h->ke_bound, h->has_force ? 0 : 1, h->stream))) return e;
-      if ((e = launch_split_collide<Real>(h, 1, p))) return e;
+      if ((e = launch_split_learned<Real>(h, p))) return e;
     } else {
       e = apply_filter ? launch_split_prologue<Real>(h, PRO_FIXED, p, LearnedPtrs<Real>{}) : launch_split_collide<Real>(h, 0, p);
       if (e) return e;

@@ -147,6 +147,14 @@ bool split_prologue_d3q19(int N, bool affine, int mode, const KParams<Real> &p, 
 template <typename Real>
 bool split_prologue_d3q27(int N, bool affine, int mode, const KParams<Real> &p, const SplitHost &h,
                           const LearnedPtrs<Real> &lp, cudaStream_t s, cudaError_t *err);
+// learned control of the split form: rho - rho0 and |u| on unique nodes into q [2][Gs] (+ the
+// drift integrals into lp.acc), element features X [E][2n], then the network -> lp.sigma_out [E][n]
+template <typename Real>
+bool split_control_d3q19(int N, const KParams<Real> &p, const SplitHost &h, const LearnedPtrs<Real> &lp, Real *q,
+                         Real *X, const double *mass, cudaStream_t s, cudaError_t *err);
+template <typename Real>
+bool split_control_d3q27(int N, const KParams<Real> &p, const SplitHost &h, const LearnedPtrs<Real> &lp, Real *q,
+                         Real *X, const double *mass, cudaStream_t s, cudaError_t *err);
 // which: 0 collision on unique nodes (writes fout -> f0out), 1 assembly of the learned
 // filter's weighted shares at shared nodes + collision
 template <typename Real>

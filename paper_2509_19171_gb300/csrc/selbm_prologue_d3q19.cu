@@ -29,4 +29,19 @@ template bool split_prologue_d3q19<float>(int, bool, int, const KParams<float> &
 template bool split_prologue_d3q19<double>(int, bool, int, const KParams<double> &, const SplitHost &,
                                           const LearnedPtrs<double> &, cudaStream_t, cudaError_t *);
 
+// learned control of the split form (node features, element network) -> lp.sigma_out
+template <typename Real>
+bool split_control_d3q19(int N, const KParams<Real> &p, const SplitHost &h, const LearnedPtrs<Real> &lp, Real *q,
+                        Real *X, const double *mass, cudaStream_t s, cudaError_t *err) {
+  switch (N) {
+    case 4: *err = launch_split_control_t<Real, SELBM_D3Q19, 5>(p, h, lp, q, X, mass, s); return true;
+    case 7: *err = launch_split_control_t<Real, SELBM_D3Q19, 8>(p, h, lp, q, X, mass, s); return true;
+  }
+  return false;
+}
+template bool split_control_d3q19<float>(int, const KParams<float> &, const SplitHost &, const LearnedPtrs<float> &,
+                                        float *, float *, const double *, cudaStream_t, cudaError_t *);
+template bool split_control_d3q19<double>(int, const KParams<double> &, const SplitHost &, const LearnedPtrs<double> &,
+                                         double *, double *, const double *, cudaStream_t, cudaError_t *);
+
 }  // namespace slb

@@ -55,8 +55,7 @@ constexpr size_t prologue_smem_bytes() {
   using TI = Tile<Real, n, 3>;
   constexpr int Q = LT<LAT>::v.Q;
   size_t reals = (size_t)Q * TI::PS + 2 * n * n;                   // tile; U, W or F_e, V^-1
-  if (MODE == PRO_LEARNED)
-    reals += 2 * (size_t)TI::PS + n * n + n + 2 * n + 2 * kHidden + 2 + (kProThreads / 32) * 2 * n;
+  if (MODE == PRO_LEARNED) reals += 2 * n * n + n;                  // V, W (or F_e^T), sigma_e
   return reals * sizeof(Real);
 }
 
@@ -218,28 +217,21 @@ __device__ __forceinline__ void tile_dense3(Real *sf, int tid, const Real *M, co
 }
 
 template <typename Real, int LAT, int n, bool AFFINE, int MODE>
-__global__ void __launch_bounds__(kProThreads, sizeof(Real) == 4 ? (MODE == PRO_LEARNED ? 3 : 4) : (MODE == PRO_LEARNED ? 1 : 2))
+__global__ void __launch_bounds__(kProThreads, sizeof(Real) == 4 ? 4 : 2)
 prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedIn<Real, n> c) {
-  constexpr int Q = LT<LAT>::v.Q, DIM = 3, Np = n * n * n, T = kProThreads, NW = T / 32, H = kHidden, nin = 2 * n;
+  constexpr int Q = LT<LAT>::v.Q, DIM = 3, Np = n * n * n, T = kProThreads;
   using TI = Tile<Real, n, DIM>;
   constexpr int PS = TI::PS;
-  constexpr VelTab V = LT<LAT>::v;
   constexpr bool LEARNED = MODE == PRO_LEARNED;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real *sf = reinterpret_cast<Real *>(smem_raw);   // [Q][PS]
   Real *sM0 = sf + Q * PS;                          // learned: [n][n] F_e or U_e^T
   Real *sM1 = sM0 + n * n;                          // learned: [n][n] V^-1
-  Real *sq = sM1 + n * n;                           // learned: [2][PS] rho - rho0, |u| -> modal
-  Real *sVm = sq + 2 * PS;                          // [n][n]
-  Real *ssig = sVm + n * n;                         // [n]
-  Real *sx = ssig + n;                              // [2n]
-  Real *h1 = sx + nin;                              // [64]
-  Real *h2 = h1 + H;                                // [64]
-  Real *so = h2 + H;                                // [2]
-  Real *spart = so + 2;                             // [NW][2n]
-  __shared__ double dred[NW][2];
-  __shared__ int s_r, in_range, s_mode[n];
-  const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  Real *sVm = sM1 + n * n;                          // learned: [n][n]
+  Real *sW = sVm + n * n;                           // learned: [n][n] W or F_e^T
+  Real *ssig = sW + n * n;                          // learned: [n] sigma_e of this element
+  __shared__ int s_r, s_mode[n];
+  const int e = blockIdx.x, tid = threadIdx.x;
   const int32_t *l2g = p.l2g + (size_t)e * Np;
   const size_t G = p.Gs;                            // population stride of the state
   auto weight = [&](int i) -> Real {
@@ -250,11 +242,12 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
     return p.wJ[(size_t)e * Np + i];
   };
   if (LEARNED) {
+    // the element's transfer function, chosen by element_sigma_kernel
     for (int k = tid; k < n * n; k += T) { sM1[k] = c.Vinv[k]; sVm[k] = c.Vm[k]; }
-    if (tid == 0) in_range = 1;
+    if (tid < n) ssig[tid] = c.sigma_out[(size_t)e * n + tid];
   }
   // ---- gather with asynchronous copies (all Q populations of the thread's nodes in
-  //      flight at once); the learned control then takes rho - rho0 and |u| at every node
+  //      flight at once)
   {
     const unsigned s_f = (unsigned)__cvta_generic_to_shared(sf);
     for (int i = tid; i < Np; i += T) {
@@ -265,126 +258,9 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
     }
     cp_async_wait_all();
   }
-  double pm = 0.0, pk = 0.0;
-  if (LEARNED) {
-    for (int i = tid; i < Np; i += T) {        // the nodes this thread copied
-      const int ti = TI::node(i);
-      Real drho = 0, j[3] = {0, 0, 0};
-      static_for<0, Q>([&](auto ac) {
-        constexpr int a = decltype(ac)::value;
-        const Real v = sf[a * PS + ti];
-        drho += v;
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) {
-          if (V.e[a][k] > 0) j[k] += v;
-          else if (V.e[a][k] < 0) j[k] -= v;
-        }
-      });
-      const Real rho = p.rho0 + drho;
-      Real uu = 0;
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) uu += (j[k] / rho) * (j[k] / rho);
-      sq[ti] = drho;
-      sq[PS + ti] = sqrt(uu);
-      if (c.acc) {
-        const double wq = (double)weight(i);
-        pm += wq * (double)rho;
-        pk += 0.5 * (double)p.rho0 * wq * (double)uu;
-      }
-    }
-  }
-  if (LEARNED && c.acc) {
-    pm = warp_sum(pm);
-    pk = warp_sum(pk);
-    if (lane == 0) { dred[wid][0] = pm; dred[wid][1] = pk; }
-  }
   __syncthreads();
 
   if (LEARNED) {
-    if (c.acc && tid == 0) {
-      double sm = 0.0, sk = 0.0;
-      for (int w = 0; w < NW; ++w) { sm += dred[w][0]; sk += dred[w][1]; }
-      atomicAdd(&c.acc[0], sm);
-      atomicAdd(&c.acc[1], sk);
-    }
-    // modal coefficients of both fields: V^-1 along every axis
-    tile_pass3<Real, n, 2, T>(sq, tid, [&](Real (&v)[n]) { dense_vals<Real, n>(v, sM1); });
-    // shell energies E_k = sum over max(k0, k1, k2) = k of the squared coefficients
-    Real en[2][n];
-#pragma unroll
-    for (int k = 0; k < n; ++k) { en[0][k] = 0; en[1][k] = 0; }
-    for (int i = tid; i < Np; i += T) {
-      const int i0 = i % n, i1 = (i / n) % n, i2 = i / (n * n);
-      const int sh = max(i0, max(i1, i2));
-      const int ti = TI::node(i);
-      const Real q0 = sq[ti], q1 = sq[PS + ti];
-#pragma unroll
-      for (int k = 0; k < n; ++k)
-        if (k == sh) { en[0][k] += q0 * q0; en[1][k] += q1 * q1; }
-    }
-#pragma unroll
-    for (int f = 0; f < 2; ++f)
-#pragma unroll
-      for (int k = 0; k < n; ++k) {
-        const Real s = warp_sum(en[f][k]);
-        if (lane == 0) spart[wid * nin + f * n + k] = s;
-      }
-    __syncthreads();
-    if (tid < nin) {
-      Real s = 0;
-      for (int w = 0; w < NW; ++w) s += spart[w * nin + tid];
-      const Real x = log10(s + Real(1e-30));
-      if (c.feat_out) c.feat_out[(size_t)e * nin + tid] = (float)x;
-      if (c.W) {
-        const Real lo = c.lo[tid], hi = c.hi[tid];
-        if (!(x >= lo && x <= hi)) in_range = 0;
-        sx[tid] = Real(2) * (x - lo) / (hi - lo) - Real(1);
-      }
-    }
-    if (!c.W) return;
-    __syncthreads();
-    const bool use_net = in_range && !(c.flag && *c.flag);
-    if (use_net) {
-      const __nv_bfloat16 *W1 = c.W, *b1 = W1 + H * nin, *W2 = b1 + H, *b2 = W2 + H * H, *W3 = b2 + H, *b3 = W3 + 2 * H;
-      for (int o = wid; o < H; o += NW) {
-        Real z = lane < nin ? (Real)__bfloat162float(W1[o * nin + lane]) * sx[lane] : Real(0);
-        z = warp_sum(z);
-        if (lane == 0) h1[o] = tanh((Real)__bfloat162float(b1[o]) + z);
-      }
-      __syncthreads();
-      for (int o = wid; o < H; o += NW) {
-        const __nv_bfloat162 w2 = reinterpret_cast<const __nv_bfloat162 *>(W2 + o * H)[lane];
-        Real z = (Real)__low2float(w2) * h1[2 * lane] + (Real)__high2float(w2) * h1[2 * lane + 1];
-        z = warp_sum(z);
-        if (lane == 0) h2[o] = tanh((Real)__bfloat162float(b2[o]) + z);
-      }
-      __syncthreads();
-      if (wid < 2) {
-        const __nv_bfloat162 w3 = reinterpret_cast<const __nv_bfloat162 *>(W3 + wid * H)[lane];
-        Real z = (Real)__low2float(w3) * h2[2 * lane] + (Real)__high2float(w3) * h2[2 * lane + 1];
-        z = warp_sum(z);
-        if (lane == 0) so[wid] = (Real)__bfloat162float(b3[wid]) + z;
-      }
-      __syncthreads();
-    } else if (tid == 0 && c.n_fallback) {
-      atomicAdd(c.n_fallback, 1);
-    }
-    if (tid < n) {
-      Real sig = c.fixed_sigma[tid];
-      if (use_net) {
-        const Real gam = Real(0.5) / (Real(1) + exp(-so[0]));
-        const Real kc = Real(2) + Real(n - 4) / (Real(1) + exp(-so[1]));
-        sig = Real(1);
-        if (tid > kc) {
-          const Real r = (Real(tid) - kc) / (Real(n - 1) - kc);
-          sig = Real(1) - gam * r * r;
-        }
-      }
-      ssig[tid] = sig;
-      if (c.sigma_out) c.sigma_out[(size_t)e * n + tid] = sig;
-    }
-    if (!c.outputs) return;
-    __syncthreads();
     // F_e = V diag(sigma) V^-1 with exact identity end rows, = I + U W with U = V[:, d]
     // diag(sigma_d - 1) (end rows zero) and W = V^-1[d, :] over the damped modes d: the
     // low-rank form when it is cheaper (2 r n < n^2 multiply-adds per line)
@@ -396,7 +272,6 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
     }
     __syncthreads();
     const int r = s_r;
-    Real *sW = sq;                                     // the modal fields are no longer needed
     if (2 * r < n) {
       for (int idx = tid; idx < n * r; idx += T) {       // U^T [q][j]
         const int q = idx / n, j = idx - q * n, k = s_mode[q];
@@ -455,6 +330,221 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
 #pragma unroll
     for (int a = 0; a < Q; ++a) p.f0out[(size_t)a * G + g] = fr[a];
     if (p.has_force) p.rho[g] = rho;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// learned control, split form: node features, then the per-element network
+// ---------------------------------------------------------------------------
+// rho - rho0 and |u| at every unique node of the state the pending filter acts on, q [2][Gs],
+// and its drift integrals sum M_g rho_g and sum M_g rho0 |u_g|^2 / 2 (added to acc[0], acc[1])
+template <typename Real, int LAT>
+__global__ void __launch_bounds__(256) node_features_kernel(const KParams<Real> p, Real *q, const double *mass,
+                                                            double *acc) {
+  constexpr VelTab V = LT<LAT>::v;
+  constexpr int Q = V.Q, DIM = V.D;
+  __shared__ double red[8][2];
+  const size_t Gs = p.Gs;
+  double pm = 0.0, pk = 0.0;
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < (size_t)p.G; g += (size_t)gridDim.x * blockDim.x) {
+    Real drho = 0, j[3] = {0, 0, 0};
+    static_for<0, Q>([&](auto ac) {
+      constexpr int a = decltype(ac)::value;
+      const Real v = p.fin[(size_t)a * Gs + g];
+      drho += v;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        if (V.e[a][k] > 0) j[k] += v;
+        else if (V.e[a][k] < 0) j[k] -= v;
+      }
+    });
+    const Real rho = p.rho0 + drho;
+    Real uu = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) uu += (j[k] / rho) * (j[k] / rho);
+    q[g] = drho;
+    q[Gs + g] = sqrt(uu);
+    if (acc) {
+      pm += mass[g] * (double)rho;
+      pk += 0.5 * (double)p.rho0 * mass[g] * (double)uu;
+    }
+  }
+  if (!acc) return;
+  pm = warp_sum(pm);
+  pk = warp_sum(pk);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { red[wid][0] = pm; red[wid][1] = pk; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sm = 0.0, sk = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sm += red[w][0]; sk += red[w][1]; }
+    atomicAdd(&acc[0], sm);
+    atomicAdd(&acc[1], sk);
+  }
+}
+
+// One warp per element (kCtlWarps elements per CTA): the fields at its local nodes, modal
+// coefficients (V^-1 along every axis), shell energies E_k (largest modal index k) and the
+// features x = log10(E_k + 1e-30) of rho - rho0 and |u| -> X [E][2n]
+constexpr int kCtlWarps = 4;
+template <typename Real, int n>
+__global__ void __launch_bounds__(32 * kCtlWarps, sizeof(Real) == 4 ? 4 : 2)
+element_features_kernel(const KParams<Real> p, const LearnedIn<Real, n> c, const Real *q, Real *X) {
+  constexpr int Np = n * n * n, NL = n * n, nin = 2 * n, WPB = kCtlWarps;
+  static_assert(nin <= 32, "one lane per feature");
+  __shared__ __align__(16) Real sq[WPB][2][Np];
+  __shared__ Real sVi[n * n];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = threadIdx.x; k < n * n; k += blockDim.x) sVi[k] = c.Vinv[k];
+  __syncthreads();                                   // the only block-wide barrier
+  const int e = blockIdx.x * WPB + wid;
+  if (e >= p.E) return;
+  const int32_t *l2g = p.l2g + (size_t)e * Np;
+  const size_t Gs = p.Gs;
+  Real *f0 = sq[wid][0], *f1 = sq[wid][1];
+  {
+    // all of the lane's index and field loads in flight together (one dependent round trip)
+    constexpr int NPL = (Np + 31) / 32, HALF = (NPL + 1) / 2;
+#pragma unroll
+    for (int r0 = 0; r0 < NPL; r0 += HALF) {
+      int32_t gi[HALF];
+#pragma unroll
+      for (int r = 0; r < HALF; ++r) {
+        const int i = lane + 32 * (r0 + r);
+        gi[r] = (r0 + r < NPL && i < Np) ? l2g[i] : 0;
+      }
+#pragma unroll
+      for (int r = 0; r < HALF; ++r) {
+        const int i = lane + 32 * (r0 + r);
+        if (r0 + r < NPL && i < Np) {
+          f0[i] = q[gi[r]];
+          f1[i] = q[Gs + gi[r]];
+        }
+      }
+    }
+  }
+  __syncwarp();
+  // modal coefficients of both fields: V^-1 along r, s and t (node order r fastest)
+#pragma unroll 1
+  for (int axis = 0; axis < 3; ++axis) {
+    const int stride = axis == 0 ? 1 : (axis == 1 ? n : NL);
+#pragma unroll 1
+    for (int t = lane; t < 2 * NL; t += 32) {
+      const int f = t / NL, L = t - f * NL;
+      const int base = axis == 0 ? L * n : (axis == 1 ? (L % n) + NL * (L / n) : L);
+      Real *row = sq[wid][f] + base;
+      Real v[n];
+#pragma unroll
+      for (int k = 0; k < n; ++k) v[k] = row[k * stride];
+      dense_vals<Real, n>(v, sVi);
+#pragma unroll
+      for (int k = 0; k < n; ++k) row[k * stride] = v[k];
+    }
+    __syncwarp();
+  }
+  // shell energies E_k = sum over max(k0, k1, k2) = k of the squared coefficients
+  Real en[2][n];
+#pragma unroll
+  for (int k = 0; k < n; ++k) { en[0][k] = 0; en[1][k] = 0; }
+  for (int i = lane; i < Np; i += 32) {
+    const int i0 = i % n, i1 = (i / n) % n, i2 = i / NL;
+    const int sh = max(i0, max(i1, i2));
+    const Real q0 = f0[i], q1 = f1[i];
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+      if (k == sh) { en[0][k] += q0 * q0; en[1][k] += q1 * q1; }
+  }
+  Real mine = 0;                                      // lane k < nin: energy k
+#pragma unroll
+  for (int f = 0; f < 2; ++f)
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      const Real sum = warp_sum(en[f][k]);
+      if (lane == f * n + k) mine = sum;
+    }
+  if (lane < nin) {
+    const Real x = log10(mine + Real(1e-30));
+    X[(size_t)e * nin + lane] = x;
+    if (c.feat_out) c.feat_out[(size_t)e * nin + lane] = (float)x;
+  }
+}
+
+// The network over kMlpEB elements per CTA (weights staged once in shared memory, every thread
+// computing independent outputs): scaled inputs s = 2 (x - lo)/(hi - lo) - 1, h1 = tanh(W1 s + b1),
+// h2 = tanh(W2 h1 + b2), o = W3 h2 + b3 (BF16 weights, Real arithmetic), then the element's
+// transfer function: the paper's quadratic filter at (gamma, kc) = (0.5 sigmoid(o0),
+// 2 + (N-3) sigmoid(o1)), or the fixed filter when a feature leaves [lo, hi] or the drift
+// fallback is on.  sigma_out [E][n].
+constexpr int kMlpThreads = 256;
+template <typename Real>
+constexpr int mlp_elements_per_cta() { return 16; }
+template <typename Real, int n>
+__global__ void __launch_bounds__(kMlpThreads) mlp_sigma_kernel(const int E, const LearnedIn<Real, n> c, const Real *X) {
+  constexpr int H = kHidden, nin = 2 * n, EB = mlp_elements_per_cta<Real>(), T = kMlpThreads;
+  __shared__ float w1[H][nin], w2[H][H + 1], w3[2][H], b1[H], b2[H], b3[2];
+  __shared__ Real sx[EB][nin], h1[EB][H], h2[EB][H], so[EB][2];
+  __shared__ int inr[EB];
+  const int tid = threadIdx.x, e0 = blockIdx.x * EB;
+  const __nv_bfloat16 *W1 = c.W, *B1 = W1 + H * nin, *W2 = B1 + H, *B2 = W2 + H * H, *W3 = B2 + H, *B3 = W3 + 2 * H;
+  for (int k = tid; k < H * nin; k += T) w1[k / nin][k % nin] = __bfloat162float(W1[k]);
+  for (int k = tid; k < H * H; k += T) w2[k / H][k % H] = __bfloat162float(W2[k]);
+  for (int k = tid; k < 2 * H; k += T) w3[k / H][k % H] = __bfloat162float(W3[k]);
+  for (int k = tid; k < H; k += T) { b1[k] = __bfloat162float(B1[k]); b2[k] = __bfloat162float(B2[k]); }
+  if (tid < 2) b3[tid] = __bfloat162float(B3[tid]);
+  if (tid < EB) inr[tid] = 1;
+  __syncthreads();
+  for (int k = tid; k < EB * nin; k += T) {
+    const int el = k / nin, i = k - el * nin, e = e0 + el;
+    Real sv = 0;
+    if (e < E) {
+      const Real x = X[(size_t)e * nin + i], lo = c.lo[i], hi = c.hi[i];
+      if (!(x >= lo && x <= hi)) atomicAnd(&inr[el], 0);
+      sv = Real(2) * (x - lo) / (hi - lo) - Real(1);
+    }
+    sx[el][i] = sv;
+  }
+  __syncthreads();
+  for (int k = tid; k < EB * H; k += T) {
+    const int el = k / H, o = k - el * H;
+    Real z = (Real)b1[o];
+#pragma unroll
+    for (int i = 0; i < nin; ++i) z += (Real)w1[o][i] * sx[el][i];
+    h1[el][o] = tanh(z);
+  }
+  __syncthreads();
+  for (int k = tid; k < EB * H; k += T) {
+    const int el = k / H, o = k - el * H;
+    Real z = (Real)b2[o];
+#pragma unroll 8
+    for (int i = 0; i < H; ++i) z += (Real)w2[o][i] * h1[el][i];
+    h2[el][o] = tanh(z);
+  }
+  __syncthreads();
+  if (tid < 2 * EB) {
+    const int el = tid >> 1, o = tid & 1;
+    Real z = (Real)b3[o];
+#pragma unroll 8
+    for (int i = 0; i < H; ++i) z += (Real)w3[o][i] * h2[el][i];
+    so[el][o] = z;
+  }
+  __syncthreads();
+  for (int k = tid; k < EB * n; k += T) {
+    const int el = k / n, j = k - el * n, e = e0 + el;
+    if (e >= E) continue;
+    const bool use_net = inr[el] && !(c.flag && *c.flag);
+    Real sig = c.fixed_sigma[j];
+    if (use_net) {
+      const Real gam = Real(0.5) / (Real(1) + exp(-so[el][0]));
+      const Real kc = Real(2) + Real(n - 4) / (Real(1) + exp(-so[el][1]));
+      sig = Real(1);
+      if (j > kc) {
+        const Real r = (Real(j) - kc) / (Real(n - 1) - kc);
+        sig = Real(1) - gam * r * r;
+      }
+    } else if (j == 0 && c.n_fallback) {
+      atomicAdd(c.n_fallback, 1);
+    }
+    c.sigma_out[(size_t)e * n + j] = sig;
   }
 }
 
@@ -572,6 +662,27 @@ cudaError_t launch_prologue_t(const KParams<Real> &p, const SplitHost &h, const 
   auto k = prologue_kernel<Real, LAT, n, AFFINE, MODE>;
   SLB_SET_SMEM_ONCE(k, smem);
   k<<<p.E, kProThreads, smem, s>>>(p, make_fast_mats<Real, n>(h), c);
+  return cudaGetLastError();
+}
+
+// learned control of the split form: node features (+ drift integrals), element features X
+// [E][2n], then the network over all elements; q: device buffer [2][Gs]
+template <typename Real, int LAT, int n>
+cudaError_t launch_split_control_t(const KParams<Real> &p, const SplitHost &h, const LearnedPtrs<Real> &lp, Real *q,
+                                   Real *X, const double *mass, cudaStream_t s) {
+  LearnedIn<Real, n> c{};
+  for (int k = 0; k < n * n; ++k) { c.Vm[k] = (Real)h.Vm[k]; c.Vinv[k] = (Real)h.Vinv[k]; }
+  for (int k = 0; k < n; ++k) c.fixed_sigma[k] = (Real)h.fixed_sigma[k];
+  c.W = lp.W; c.lo = lp.lo; c.hi = lp.hi; c.flag = lp.flag; c.acc = lp.acc; c.sigma_out = lp.sigma_out;
+  c.feat_out = lp.feat_out; c.n_fallback = lp.n_fallback; c.outputs = lp.outputs;
+  const int blocks = (int)std::min<size_t>(((size_t)p.G + 255) / 256, 152 * 8);
+  node_features_kernel<Real, LAT><<<blocks, 256, 0, s>>>(p, q, mass, lp.acc);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  element_features_kernel<Real, n><<<(p.E + kCtlWarps - 1) / kCtlWarps, 32 * kCtlWarps, 0, s>>>(p, c, q, X);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  constexpr int EB = mlp_elements_per_cta<Real>();
+  mlp_sigma_kernel<Real, n><<<(p.E + EB - 1) / EB, kMlpThreads, 0, s>>>(p.E, c, X);
   return cudaGetLastError();
 }
 
