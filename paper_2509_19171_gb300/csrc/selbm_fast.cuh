@@ -30,8 +30,70 @@ struct FastMats {
   Real U[n * n];
   Real W[n * n];
   Real w[n];
+  // even-odd form of D_hat for even n (see deriv_line): pairs (P_jk, M_jk), j, k < n/2
+  Real PM[(n / 2) * (n / 2) * 2 + 2];
   int r;
 };
+
+// The GLL nodes are symmetric about 0, so D_hat[n-1-j][n-1-k] = -D_hat[j][k].  With
+// P_jk = (D_jk + D_j,n-1-k) / 2 and M_jk = (D_jk - D_j,n-1-k) / 2 (j, k < n/2, formed in FP64)
+// the product d = D_hat v of an even-length line is d_j = P e + M o, d_{n-1-j} = M o - P e with
+// e_k = v_k + v_{n-1-k}, o_k = v_k - v_{n-1-k}: n^2/2 multiply-adds instead of n^2.
+template <typename Real, int n>
+void fill_even_odd(FastMats<Real, n> &m, const double *D) {
+  constexpr int H = n / 2;
+  for (int j = 0; j < H; ++j)
+    for (int k = 0; k < H; ++k) {
+      m.PM[(j * H + k) * 2] = (Real)(0.5 * (D[j * n + k] + D[j * n + n - 1 - k]));
+      m.PM[(j * H + k) * 2 + 1] = (Real)(0.5 * (D[j * n + k] - D[j * n + n - 1 - k]));
+    }
+}
+
+// d = D_hat v along one line: the even-odd form for even n (FP32: the P and M sums of an output
+// pair as one packed FMA chain), the dense product for odd n
+template <typename Real, int n>
+__device__ __forceinline__ void deriv_line(const FastMats<Real, n> &m, const Real (&v)[n], Real (&d)[n]) {
+  if constexpr (n % 2 == 0) {
+    constexpr int H = n / 2;
+    if constexpr (sizeof(Real) == 4) {
+      float2 eo[H];
+#pragma unroll
+      for (int k = 0; k < H; ++k) eo[k] = make_float2(v[k] + v[n - 1 - k], v[k] - v[n - 1 - k]);
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        float2 acc = __fmul2_rn(make_float2(m.PM[j * H * 2], m.PM[j * H * 2 + 1]), eo[0]);
+#pragma unroll
+        for (int k = 1; k < H; ++k)
+          acc = __ffma2_rn(make_float2(m.PM[(j * H + k) * 2], m.PM[(j * H + k) * 2 + 1]), eo[k], acc);
+        d[j] = acc.x + acc.y;
+        d[n - 1 - j] = acc.y - acc.x;
+      }
+    } else {
+      Real ev[H], od[H];
+#pragma unroll
+      for (int k = 0; k < H; ++k) { ev[k] = v[k] + v[n - 1 - k]; od[k] = v[k] - v[n - 1 - k]; }
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        Real sp = m.PM[j * H * 2] * ev[0], sm = m.PM[j * H * 2 + 1] * od[0];
+#pragma unroll
+        for (int k = 1; k < H; ++k) {
+          sp += m.PM[(j * H + k) * 2] * ev[k];
+          sm += m.PM[(j * H + k) * 2 + 1] * od[k];
+        }
+        d[j] = sp + sm;
+        d[n - 1 - j] = sm - sp;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+      Real s = 0;
+#pragma unroll
+      for (int k = 0; k < n; ++k) s += m.D[j * n + k] * v[k];
+      d[j] = s;
+    }
+  }
+}
 
 template <typename Real, int n, int DIM>
 struct Tile {
@@ -366,13 +428,10 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
         const Real c0 = scoef[a * DIM + 0], c1 = scoef[a * DIM + 1];
         const Real c2 = DIM == 3 ? scoef[a * DIM + 2] : Real(0);
         if (c0 != Real(0)) {
+          Real d[n];
+          deriv_line<Real, n>(m, v, d);
 #pragma unroll
-          for (int j = 0; j < n; ++j) {
-            Real d = 0;
-#pragma unroll
-            for (int k = 0; k < n; ++k) d += m.D[j * n + k] * v[k];
-            adv[j] = c0 * d;
-          }
+          for (int j = 0; j < n; ++j) adv[j] = c0 * d[j];
         }
         if (c1 != Real(0)) {
 #pragma unroll KU
@@ -409,12 +468,11 @@ stage_fast_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
             if (ek[k] != 0) c += ek[k] > 0 ? gm[k] : -gm[k];
           return c;
         };
+        {
+          Real d[n];
+          deriv_line<Real, n>(m, v, d);
 #pragma unroll
-        for (int j = 0; j < n; ++j) {
-          Real d = 0;
-#pragma unroll
-          for (int k = 0; k < n; ++k) d += m.D[j * n + k] * v[k];
-          adv[j] = coef(j, 0) * d;
+          for (int j = 0; j < n; ++j) adv[j] = coef(j, 0) * d[j];
         }
         {
           Real d[n];
@@ -536,6 +594,7 @@ cudaError_t launch_fast_t(const KParams<Real> &p, const double *D, const double 
   for (int k = 0; k < n * n; ++k) { m.D[k] = (Real)D[k]; m.U[k] = (Real)U[k]; m.W[k] = (Real)W[k]; }
   for (int k = 0; k < n; ++k) m.w[k] = (Real)w[k];
   m.r = r;
+  fill_even_odd(m, D);
   const size_t smem = fast_smem_bytes<Real, LAT, n, AFFINE>(p.wall_max);
   auto k = stage_fast_kernel<Real, LAT, n, AFFINE>;
   static thread_local int attr_dev = -1;

@@ -155,6 +155,57 @@ __device__ __forceinline__ void filter_rows(Real (&v)[n], const Real *UT, const 
   for (int j = 0; j < n; ++j) v[j] = o[j];
 }
 
+// y <- ((I + U W) x (I + U W) x (I + U W)) y on NP populations of a tile, U^T and W (r rows of
+// n) in shared memory.  On the swizzled FP32 tile the s- and t-passes take two adjacent columns
+// per task and share each row of U^T and W between them (packed FMAs).
+template <typename Real, int n, int NP, int T>
+__device__ __forceinline__ void tile_lowrank3(Real *sf, int tid, const Real *UT, const Real *W, int r) {
+  using TI = Tile<Real, n, 3>;
+  if constexpr (!TI::SW) {
+    tile_pass3<Real, n, NP, T>(sf, tid, [&](Real (&v)[n]) { filter_rows<Real, n>(v, UT, W, r); });
+  } else {
+    constexpr int NL = n * n, PS = TI::PS;
+    for (int t = tid; t < NP * NL; t += T) {          // r-lines
+      const int a = t / NL, L = t - a * NL;
+      const int i1 = L % n, i2 = L / n;
+      Real v[n];
+      Real *base = sf + a * PS + TI::line(i1, i2);
+      load_line<Real, n>(base, TI::sw(i1), v);
+      filter_rows<Real, n>(v, UT, W, r);
+      store_line<Real, n>(base, TI::sw(i1), v);
+    }
+    __syncthreads();
+    auto pair_pass = [&](auto addr) {
+      for (int t = tid; t < NP * NL / 2; t += T) {
+        const int a = t / (NL / 2), rr = t - a * (NL / 2), q = rr & 3, w = rr >> 2;
+        Real *base = sf + a * PS;
+        float2 v2[n], o2[n];
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+          v2[k] = *reinterpret_cast<const float2 *>(base + addr(w, k, q));
+          o2[k] = v2[k];
+        }
+        for (int m = 0; m < r; ++m) {
+          Real row[n];
+          load_line<Real, n>(W + m * n, 0, row);
+          float2 s2 = __fmul2_rn(make_float2(row[0], row[0]), v2[0]);
+#pragma unroll
+          for (int k = 1; k < n; ++k) s2 = __ffma2_rn(make_float2(row[k], row[k]), v2[k], s2);
+          load_line<Real, n>(UT + m * n, 0, row);
+#pragma unroll
+          for (int j = 0; j < n; ++j) o2[j] = __ffma2_rn(make_float2(row[j], row[j]), s2, o2[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < n; ++j) *reinterpret_cast<float2 *>(base + addr(w, j, q)) = o2[j];
+      }
+    };
+    pair_pass([](int w, int k, int q) { return TI::line(k, w) + ((2 * q) ^ TI::sw(k)); });
+    __syncthreads();
+    pair_pass([](int w, int k, int q) { return TI::line(w, k) + ((2 * q) ^ TI::sw(w)); });
+    __syncthreads();
+  }
+}
+
 template <typename Real, int n>
 __device__ __forceinline__ void dense_vals(Real (&v)[n], const Real *M) {
   Real o[n];
@@ -282,7 +333,7 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
         sW[q * n + jj] = sM1[s_mode[q] * n + jj];
       }
       __syncthreads();
-      tile_pass3<Real, n, Q, T>(sf, tid, [&](Real (&v)[n]) { filter_rows<Real, n>(v, sM0, sW, r); });
+      tile_lowrank3<Real, n, Q, T>(sf, tid, sM0, sW, r);
     } else {
       for (int k = tid; k < n * n; k += T) {
         const int rr = k / n, jj = k - rr * n;
@@ -621,6 +672,7 @@ FastMats<Real, n> make_fast_mats(const SplitHost &h) {
   for (int k = 0; k < n * n; ++k) { m.D[k] = (Real)h.D[k]; m.U[k] = (Real)h.U[k]; m.W[k] = (Real)h.W[k]; }
   for (int k = 0; k < n; ++k) m.w[k] = (Real)h.w[k];
   m.r = h.r;
+  fill_even_odd(m, h.D);
   return m;
 }
 

@@ -261,14 +261,30 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
         const Real A = use_f0 ? p.A : Real(0);
         const bool k0 = acc || (use_f0 && oin && xp > 0), k1 = acc || (use_f0 && oin && xp + 1 < n - 1);
         const Real a0 = acc ? Real(1) : A;
+        // D_hat along the axis for both lines at once, in the even-odd form (see deriv_line)
+        constexpr int H = n / 2;
+        float2 ev[H], od[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+          const float2 lo = *reinterpret_cast<const float2 *>(fa + (AX == 1 ? TI::at(xp, k, o) : TI::at(xp, o, k)));
+          const float2 hi =
+              *reinterpret_cast<const float2 *>(fa + (AX == 1 ? TI::at(xp, n - 1 - k, o) : TI::at(xp, o, n - 1 - k)));
+          ev[k] = __fadd2_rn(lo, hi);
+          od[k] = __fadd2_rn(lo, make_float2(-hi.x, -hi.y));
+        }
         float2 d[n];
 #pragma unroll
-        for (int j = 0; j < n; ++j) d[j] = make_float2(0.f, 0.f);
+        for (int j = 0; j < H; ++j) {
+          const float P0 = m.PM[j * H * 2], M0 = m.PM[j * H * 2 + 1];
+          float2 sp = __fmul2_rn(make_float2(P0, P0), ev[0]), sm = __fmul2_rn(make_float2(M0, M0), od[0]);
 #pragma unroll
-        for (int k = 0; k < n; ++k) {
-          const float2 vk = *reinterpret_cast<const float2 *>(fa + (AX == 1 ? TI::at(xp, k, o) : TI::at(xp, o, k)));
-#pragma unroll
-          for (int j = 0; j < n; ++j) d[j] = __ffma2_rn(make_float2(m.D[j * n + k], m.D[j * n + k]), vk, d[j]);
+          for (int k = 1; k < H; ++k) {
+            const float P = m.PM[(j * H + k) * 2], M = m.PM[(j * H + k) * 2 + 1];
+            sp = __ffma2_rn(make_float2(P, P), ev[k], sp);
+            sm = __ffma2_rn(make_float2(M, M), od[k], sm);
+          }
+          d[j] = __fadd2_rn(sp, sm);
+          d[n - 1 - j] = __fadd2_rn(sm, make_float2(-sp.x, -sp.y));
         }
         const float2 cc = make_float2(c, c);
 #pragma unroll
@@ -339,13 +355,10 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
             }
         }
         if (c0 != Real(0)) {
+          Real d[n];
+          deriv_line<Real, n>(m, v, d);
 #pragma unroll
-          for (int j = 0; j < n; ++j) {
-            Real d = 0;
-#pragma unroll
-            for (int k = 0; k < n; ++k) d += m.D[j * n + k] * v[k];
-            acc[j] += cr[j] * d;
-          }
+          for (int j = 0; j < n; ++j) acc[j] += cr[j] * d[j];
         }
         Real wl[n];                                           // wJ of the line's nodes
         if constexpr (AFFINE) {
@@ -415,13 +428,10 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
       if (AFFINE) {
         const Real c0 = cf[pl * DIM + 0], c1 = cf[pl * DIM + 1], c2 = cf[pl * DIM + 2];
         if (c0 != Real(0)) {
+          Real d[n];
+          deriv_line<Real, n>(m, v, d);
 #pragma unroll
-          for (int j = 0; j < n; ++j) {
-            Real d = 0;
-#pragma unroll
-            for (int k = 0; k < n; ++k) d += m.D[j * n + k] * v[k];
-            adv[j] = c0 * d;
-          }
+          for (int j = 0; j < n; ++j) adv[j] = c0 * d[j];
         }
         if (c1 != Real(0)) {
           Real dr[n];
@@ -452,12 +462,11 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
           const Real *gm = sg + (L * n + j) * 9 + l * DIM;
           return -Bdt * (ek[0] * gm[0] + ek[1] * gm[1] + ek[2] * gm[2]);
         };
+        {
+          Real d[n];
+          deriv_line<Real, n>(m, v, d);
 #pragma unroll
-        for (int j = 0; j < n; ++j) {
-          Real d = 0;
-#pragma unroll
-          for (int k = 0; k < n; ++k) d += m.D[j * n + k] * v[k];
-          adv[j] = coef(j, 0) * d;
+          for (int j = 0; j < n; ++j) adv[j] = coef(j, 0) * d[j];
         }
         {
           Real d[n], dr[n];
