@@ -81,7 +81,7 @@ __device__ __forceinline__ void cp_async_s(unsigned dst, const Real *src) {
 // one Runge-Kutta stage for PB populations of one element
 // ---------------------------------------------------------------------------
 template <typename Real, int LAT, int n, bool AFFINE, int PBW = 0>
-__global__ void __launch_bounds__(SplitShape<LAT, n, PBW>::THREADS, (sizeof(Real) == 4 ? (PBW > 8 ? 4 : (AFFINE ? 5 : 4)) : 2))
+__global__ void __launch_bounds__(SplitShape<LAT, n, PBW>::THREADS, (sizeof(Real) == 4 ? (PBW == 9 ? 5 : (PBW > 8 ? 4 : (AFFINE ? 5 : 4))) : 2))
 stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   using S = SplitShape<LAT, n, PBW>;
   constexpr int Q = S::Q, DIM = 3, Np = S::Np, NL = S::NL, T = S::THREADS, PB = S::PB, NG = S::NG;
