@@ -5,7 +5,8 @@ steps; at checkpoints the node RMS and max of |u - u_fp64| / U0 and of
 |rho - rho_fp64| are recorded, with the kinetic energy and dissipation histories
 (selbm_diagnostics).  Taylor-Green 16^3 N=7 D3Q27 to t = 5 L0/U0 with pointwise
 comparisons at t = 2 and 5 L0/U0 (before the chaotic decorrelation of the transition),
-the learned control also against the fixed filter it replaces; the butterfly pipe
+the learned control also against the fixed filter it replaces and, for its arithmetic
+error, against the FP64 form with the same control ("fp64_learned"); the butterfly pipe
 (8192 hexes, N=7, D3Q19, curved walls, body force) for 1000 steps, the double
 shear layer (32^2, N=8, D2Q9) for 2000 steps.
 
@@ -56,7 +57,7 @@ def run_case(case, forms, steps, checkpoints, history_every, learned=None):
         h.init_from(case.init)
         if f == "fp64_perturbed":
             perturb_fp32_level(h, case.rho0)
-        if f == "fp32dev_learned":
+        if f.endswith("_learned"):
             w = np.load(learned)
             h.set_learned_filter(w["params"], w["lo"], w["hi"], mass_bound=1e-6)
         handles[f] = h
@@ -82,6 +83,11 @@ def run_case(case, forms, steps, checkpoints, history_every, learned=None):
                 row["learned_status"] = handles["fp32dev_learned"].learned_status()
                 if "fp32dev" in fields:
                     row["learned_vs_fixed"] = _errors(fields["fp32dev_learned"], fields["fp32dev"], case.U0)
+                if "fp64_learned" in fields:
+                    # the arithmetic error of the learned form: FP32 against FP64 with the same control
+                    row["learned_fp32_vs_learned_fp64"] = _errors(fields["fp32dev_learned"], fields["fp64_learned"],
+                                                                  case.U0)
+                    row["learned_fp64_status"] = handles["fp64_learned"].learned_status()
             errs.append(row)
     out = {"case": case.name, "elements": case.mesh.nelem, "order": case.order, "lattice": case.lattice,
            "U0": case.U0, "steps": steps, "dt": handles["fp64"].dt, "wall_s": round(time.time() - t0, 1),
@@ -116,13 +122,14 @@ def main():
     weights = args.weights
     tgv = W.tgv3d_case()
     tgv_steps = 200 if args.quick else 8000     # t = 5 L0/U0 at dt = 0.0126
-    forms = ["fp64", "fp64_perturbed", "fp32dev"] + (["fp32dev_learned"] if os.path.exists(weights) else [])
+    lforms = ["fp64_learned", "fp32dev_learned"] if os.path.exists(weights) else []
+    forms = ["fp64", "fp64_perturbed", "fp32dev"] + lforms
     if "tgv" in cases:
         res.append(run_case(tgv, forms, tgv_steps, [tgv_steps * 2 // 5, tgv_steps], max(tgv_steps // 40, 1), weights))
     if "pipe" in cases:
         pipe = W.pipe_case()
         pipe_steps = 100 if args.quick else 1000
-        pforms = ["fp64", "fp64_perturbed", "fp32dev"] + (["fp32dev_learned"] if os.path.exists(weights) else [])
+        pforms = ["fp64", "fp64_perturbed", "fp32dev"] + lforms
         res.append(run_case(pipe, pforms, pipe_steps, [pipe_steps], max(pipe_steps // 10, 1), weights))
     if "shear" in cases:
         shear = W.shear_layer_case()
