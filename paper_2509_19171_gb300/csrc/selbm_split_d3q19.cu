@@ -9,12 +9,13 @@ bool split_stage_d3q19(int N, bool affine, const KParams<Real> &p, const SplitHo
   switch (N) {
     case 4: *err = affine ? launch_split_t<Real, SELBM_D3Q19, 5, true>(p, h, s) : launch_split_t<Real, SELBM_D3Q19, 5, false>(p, h, s); return true;
     case 7:
-      // FP32 on affine elements: 10 populations per work item, one warp each (no idle warps)
-      if constexpr (std::is_same<Real, float>::value)
-        if (affine) {
-          *err = launch_split_t<Real, SELBM_D3Q19, 8, true, 10>(p, h, s);
-          return true;
-        }
+      // FP32: 10 populations per work item, one warp each (no idle warps); on curved elements
+      // two work items per element also halve the re-reads of the per-node metrics
+      if constexpr (std::is_same<Real, float>::value) {
+        *err = affine ? launch_split_t<Real, SELBM_D3Q19, 8, true, 10>(p, h, s)
+                      : launch_split_t<Real, SELBM_D3Q19, 8, false, 10>(p, h, s);
+        return true;
+      }
       *err = affine ? launch_split_t<Real, SELBM_D3Q19, 8, true>(p, h, s) : launch_split_t<Real, SELBM_D3Q19, 8, false>(p, h, s);
       return true;
   }

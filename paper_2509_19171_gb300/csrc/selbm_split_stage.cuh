@@ -31,11 +31,20 @@ struct SplitShape {
   static constexpr int NPT = (Np + THREADS - 1) / THREADS;        // nodes per thread when gathering
 };
 
+// offset (in values) of the curved-element metric planes: 16-byte aligned, since the passes read
+// them with 8- and 16-byte vector loads
+template <typename Real, int LAT, int n, int PBW = 0>
+constexpr size_t split_sg_offset() {
+  using S = SplitShape<LAT, n, PBW>;
+  using TI = Tile<Real, n, 3>;
+  constexpr size_t V16 = 16 / sizeof(Real);
+  return (2 * (size_t)S::PB * TI::PS + n * n + S::PB * 3 + 2 * S::PB + n + V16 - 1) / V16 * V16;
+}
+
 template <typename Real, int LAT, int n, bool AFFINE, int PBW = 0>
 constexpr size_t split_smem_bytes(int wall_max) {
   using S = SplitShape<LAT, n, PBW>;
-  using TI = Tile<Real, n, 3>;
-  size_t reals = 2 * (size_t)S::PB * TI::PS + n * n + S::PB * 3 + 2 * S::PB + n;
+  size_t reals = split_sg_offset<Real, LAT, n, PBW>();
   if (!AFFINE) reals += (size_t)S::Np * 10;
   reals += (size_t)S::PB * wall_max;
   return reals * sizeof(Real);
@@ -81,7 +90,7 @@ __device__ __forceinline__ void cp_async_s(unsigned dst, const Real *src) {
 // one Runge-Kutta stage for PB populations of one element
 // ---------------------------------------------------------------------------
 template <typename Real, int LAT, int n, bool AFFINE, int PBW = 0>
-__global__ void __launch_bounds__(SplitShape<LAT, n, PBW>::THREADS, (sizeof(Real) == 4 ? (PBW == 9 ? 5 : (PBW > 8 ? 4 : (AFFINE ? 5 : 4))) : 2))
+__global__ void __launch_bounds__(SplitShape<LAT, n, PBW>::THREADS, (sizeof(Real) == 4 ? (AFFINE ? (PBW > 9 ? 4 : 5) : (PBW > 0 ? 3 : 4)) : 2))
 stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   using S = SplitShape<LAT, n, PBW>;
   constexpr int Q = S::Q, DIM = 3, Np = S::Np, NL = S::NL, T = S::THREADS, PB = S::PB, NG = S::NG;
@@ -100,7 +109,8 @@ stage_split_kernel(const KParams<Real> p, const FastMats<Real, n> m) {
   Real *cf = sD + n * n;                            // [PB][DIM] (affine: -B dt sum_k e_k dr_l/dx_k)
   Real *fc = cf + PB * DIM;                         // [2][PB]   B dt F*_a / rho; B dt 3 t_a
   Real *sw = fc + 2 * PB;                           // [n]
-  Real *sg = sw + n;                                // curved: dr_l/dx_k [Np][9], wJ [Np]
+  Real *sg = sf + split_sg_offset<Real, LAT, n, PBW>();   // curved: dr_l/dx_k [Np][9], wJ [Np]
+  static_assert(split_sg_offset<Real, LAT, n, PBW>() * sizeof(Real) % 16 == 0, "metric planes 16-byte aligned");
   Real *wbuf = sg + (AFFINE ? 0 : Np * 10);         // [wall nodes][PB]
   const int e = blockIdx.x / NG, a0 = (blockIdx.x - e * NG) * PB;
   const int na = Q - a0 < PB ? Q - a0 : PB;

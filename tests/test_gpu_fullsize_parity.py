@@ -108,3 +108,31 @@ def test_fullsize_fp32_learned(P, full):
     assert st["fixed_element_steps"] == 0 and st["fallback_flag"] == 0
     assert s.sync() == 0
     s.close()
+
+
+def _one_step_both_precisions(P, case, tol32):
+    """FP64 and FP32 (fixed filter) one step from the case's own initial fields, every output
+    against the oracle's step."""
+    o = OracleSELBM(case.mesh, case.lattice, case.order, case.nu, cfl=case.cfl, rho0=case.rho0,
+                    filt=case.filt, body_accel=case.body_accel)
+    f = o.initial_state_from(case.init)
+    ref = o.to_local(o.step(f))
+    for prec, tol in ((P.FP64, 1e-12), (P.FP32DEV, tol32)):
+        s = P.from_case(case, precision=prec)
+        assert s.G == o.G and abs(s.dt - o.dt) < 1e-15
+        s.set_state(np.ascontiguousarray(o.to_local(f)))
+        s.step(1)
+        assert rel(s.get_state(), ref) <= tol, prec
+        s.close()
+
+
+def test_fullsize_pipe(P):
+    """The butterfly pipe at its full size (8192 curved hexes, N = 7, D3Q19, body force, flux
+    bounce-back walls): one step in FP64 (1e-12) and in FP32 deviations (1e-6)."""
+    _one_step_both_precisions(P, W.pipe_case(), 1e-6)
+
+
+def test_fullsize_shear_layer(P):
+    """The double shear layer at its full size (32^2 quads, N = 8, D2Q9, exponential filter,
+    whole-element step): one step in FP64 (1e-12) and in FP32 deviations (1e-6)."""
+    _one_step_both_precisions(P, W.shear_layer_case(), 1e-6)
