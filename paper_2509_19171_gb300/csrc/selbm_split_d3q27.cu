@@ -9,12 +9,13 @@ bool split_stage_d3q27(int N, bool affine, const KParams<Real> &p, const SplitHo
   switch (N) {
     case 5: *err = affine ? launch_split_t<Real, SELBM_D3Q27, 6, true>(p, h, s) : launch_split_t<Real, SELBM_D3Q27, 6, false>(p, h, s); return true;
     case 7:
-      // FP32 on affine elements: 9 populations per work item, one warp each (no idle warps)
-      if constexpr (std::is_same<Real, float>::value)
-        if (affine) {
-          *err = launch_split_t<Real, SELBM_D3Q27, 8, true, 9>(p, h, s);
-          return true;
-        }
+      // FP32: 9 populations per work item, one warp each (no idle warps); on curved elements
+      // three work items per element instead of four also cut the re-reads of the metrics
+      if constexpr (std::is_same<Real, float>::value) {
+        *err = affine ? launch_split_t<Real, SELBM_D3Q27, 8, true, 9>(p, h, s)
+                      : launch_split_t<Real, SELBM_D3Q27, 8, false, 9>(p, h, s);
+        return true;
+      }
       *err = affine ? launch_split_t<Real, SELBM_D3Q27, 8, true>(p, h, s) : launch_split_t<Real, SELBM_D3Q27, 8, false>(p, h, s);
       return true;
   }

@@ -73,12 +73,14 @@ def test_nodes_curved_fp64(P, lat, N):
     assert np.abs(s.node_coords().reshape(o.E, o.Np, 3) - o.X).max() < 1e-13
 
 
-def test_nodes_curved_fp32_split(P):
-    """FP32 deviations, D3Q19 N = 7: the population-split step on curved elements."""
+@pytest.mark.parametrize("lat", ["D3Q19", "D3Q27"])
+def test_nodes_curved_fp32_split(P, lat):
+    """FP32 deviations, N = 7: the population-split step on curved elements (groups of 10 / 9
+    populations with the per-node metric planes)."""
     nm = deformed_box()
     filt = {"shape": 0, "gamma": 0.1, "kc": 5.0}
-    o = OracleSELBM(nm, "D3Q19", 7, 2e-3, filt=filt)
-    s = P.SELBM(nm, "D3Q19", 7, 2e-3, precision=P.FP32DEV, filt=filt)
+    o = OracleSELBM(nm, lat, 7, 2e-3, filt=filt)
+    s = P.SELBM(nm, lat, 7, 2e-3, precision=P.FP32DEV, filt=filt)
     assert s.split
     f = random_state(o, 0.02, 4)
     s.set_state(np.ascontiguousarray(o.to_local(f)))
