@@ -14,8 +14,11 @@
 // r-line) tasks covers them, and several CTAs per SM overlap their gathers with
 // each other's arithmetic.
 //
-// With the learned control, copies of a shared node are filtered by different
-// element filters; the prologue writes their weighted shares wJ f to the trace and
+// With the learned control, three kernels choose each element's transfer function first
+// (node_features_kernel: rho - rho0, |u| and the drift integrals on unique nodes;
+// element_features_kernel: modal shell energies, one warp per element; mlp_sigma_kernel: the
+// network over 16 elements per CTA).  Copies of a shared node are then filtered by different
+// element filters: the prologue writes their weighted shares wJ f to the trace and
 // dss_collide_kernel forms the mass-weighted average and collides it.
 #pragma once
 #include <cuda_bf16.h>
@@ -293,7 +296,7 @@ prologue_kernel(const KParams<Real> p, const FastMats<Real, n> m, const LearnedI
     return p.wJ[(size_t)e * Np + i];
   };
   if (LEARNED) {
-    // the element's transfer function, chosen by element_sigma_kernel
+    // the element's transfer function, chosen by the control kernels (mlp_sigma_kernel)
     for (int k = tid; k < n * n; k += T) { sM1[k] = c.Vinv[k]; sVm[k] = c.Vm[k]; }
     if (tid < n) ssig[tid] = c.sigma_out[(size_t)e * n + tid];
   }
